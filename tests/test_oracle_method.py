@@ -1,0 +1,262 @@
+"""Pins of the oracle's method steps: closed forms, invariants and brute force on tiny inputs.
+
+Each test would fail on a plausible slip in the oracle (a dropped term, a wrong sign or
+index, a transposed operand, a missing normalisation).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cola, cosmology, fft, ics, pm, power
+
+BOX = 256.0
+
+
+def plane_wave_field(n, amps):
+    """delta_k for delta(q) = sum A cos(2 pi m.q / N) with integer index vectors m."""
+    dk = np.zeros((n, n, n), complex)
+    for (mx, my, mz), a in amps:
+        dk[mz % n, my % n, mx % n] += a * n ** 3 / 2
+        dk[-mz % n, -my % n, -mx % n] += a * n ** 3 / 2
+    return dk
+
+
+# --- Gaussian field (§5) -----------------------------------------------------------------
+
+def test_gaussian_field_hermitian_and_masked():
+    n = 16
+    pk = cosmology.linear_pk(0.3, 0.7, 0.96, 0.8)
+    dk = ics.gaussian_field(n, BOX, 7, pk)
+    real = fft.ifftn(dk)
+    assert np.abs(real.imag).max() < 1e-14 * np.abs(real.real).max()
+    assert dk[0, 0, 0] == 0
+    h = n // 2
+    assert np.all(dk[h] == 0) and np.all(dk[:, h] == 0) and np.all(dk[:, :, h] == 0)
+
+
+def test_gaussian_field_power_statistics():
+    # <|delta_k|^2> = N^6 P(k) / L^3: the mean ratio over ~N^3/2 independent modes is 1 +- a few sqrt(1/modes).
+    n = 32
+    pk = cosmology.linear_pk(0.3, 0.7, 0.96, 0.8)
+    dk = ics.gaussian_field(n, BOX, 3, pk)
+    kx, ky, kz, nyq = ics.wavevectors(n, BOX)
+    k = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    sel = (k > 0) & ~nyq
+    ratio = np.abs(dk[sel]) ** 2 / (n ** 6 * pk(k[sel]) / BOX ** 3)
+    nind = sel.sum() / 2
+    assert abs(ratio.mean() - 1) < 5 / math.sqrt(nind)
+    # |g|^2 = -ln(u1) is exponential with unit mean: its variance is 1 as well.
+    assert abs(ratio.var() - 1) < 10 / math.sqrt(nind)
+
+
+def test_gaussian_field_seed_determinism():
+    pk = cosmology.linear_pk(0.3, 0.7, 0.96, 0.8)
+    a = ics.gaussian_field(8, BOX, 11, pk)
+    b = ics.gaussian_field(8, BOX, 11, pk)
+    c = ics.gaussian_field(8, BOX, 12, pk)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+# --- 2LPT (§2.1) ------------------------------------------------------------------------
+
+def test_zeldovich_plane_wave_exact_and_no_2lpt_source():
+    n, amp = 16, 0.3
+    dk = plane_wave_field(n, [((1, 0, 0), amp)])
+    psi1, psi2 = ics.lpt_displacements(dk, BOX)
+    k1 = 2 * math.pi / BOX
+    qx = np.arange(n) * BOX / n
+    expect = -(amp / k1) * np.sin(k1 * qx)                    # div Psi1 = -delta (Eq. za)
+    assert np.abs(psi1[0] - expect[None, None, :]).max() < 1e-12 * abs(amp / k1)
+    assert np.abs(psi1[1]).max() < 1e-14 and np.abs(psi1[2]).max() < 1e-14
+    assert np.abs(psi2).max() < 1e-12                           # one plane wave: S = 0
+
+
+def test_2lpt_two_mode_source_analytic():
+    # delta = A cos(k1.q) + B cos(k2.q), k1 = (c,0,0), k2 = (a,b,0):
+    # S = phi_xx phi_yy - phi_xy^2 = A B b^2/|k2|^2 cos(k1.q) cos(k2.q); Psi2 = grad phi2, lap phi2 = S.
+    n, A, B = 8, 0.2, 0.15
+    dk = plane_wave_field(n, [((1, 0, 0), A), ((1, 2, 0), B)])
+    _, psi2 = ics.lpt_displacements(dk, BOX)
+    kf = 2 * math.pi / BOX
+    k1 = np.array([1.0, 0, 0]) * kf
+    k2 = np.array([1.0, 2.0, 0]) * kf
+    coef = A * B * k2[1] ** 2 / (k2 @ k2) / 2
+    g = np.arange(n) * BOX / n
+    qz, qy, qx = np.meshgrid(g, g, g, indexing="ij")
+    expect = np.zeros((3, n, n, n))
+    for kk in (k1 + k2, k1 - k2):             # cos a cos b = (cos(a+b) + cos(a-b)) / 2
+        phase = kk[0] * qx + kk[1] * qy + kk[2] * qz
+        for j in range(3):                    # phi2 = -coef cos/|K|^2 -> grad = coef K sin / |K|^2
+            expect[j] += coef * kk[j] * np.sin(phase) / (kk @ kk)
+    assert np.abs(psi2 - expect).max() < 1e-12 * np.abs(expect).max()
+
+
+# --- Fixed-point CIC (§2.4 step 1) ---------------------------------------------------------
+
+def bruteforce_deposit(u, nm):
+    rho = np.zeros((nm, nm, nm), dtype=np.int64)
+    for p in u:
+        cell, frac = [], []
+        for d in range(3):
+            c = math.floor(p[d])
+            fq = int(np.rint((p[d] - c) * 32768))
+            if fq == 32768:
+                c, fq = c + 1, 0
+            cell.append(c % nm)
+            frac.append(fq)
+        for dz, dy, dx in itertools.product((0, 1), repeat=3):
+            w = 1
+            for d, o in zip(range(3), (dx, dy, dz)):
+                w *= frac[d] if o else 32768 - frac[d]
+            rho[(cell[2] + dz) % nm, (cell[1] + dy) % nm, (cell[0] + dx) % nm] += w
+    return rho
+
+
+def test_cic_deposit_bruteforce_and_mass():
+    nm = 8
+    rng = np.random.default_rng(4)
+    u = rng.uniform(0, nm, size=(50, 3))
+    u[0] = [0.0, 7.9999999, 3.5]            # carry (rounds up to the next cell, wraps)
+    u[1] = [2.0, 2.0, 2.0]                  # on a node
+    u[2] = [1.0 + 0.5 / 32768, 4.25, 6.0]   # exact half-step tie -> round half to even
+    rho = pm.cic_deposit(u, nm)
+    assert np.array_equal(rho, bruteforce_deposit(u, nm))
+    assert rho.sum() == len(u) << 45
+    single = pm.cic_deposit(u[1:2], nm)
+    assert single[2, 2, 2] == 1 << 45 and np.count_nonzero(single) == 1
+
+
+def test_cic_quantise_tie_and_carry():
+    c, fq = pm.quantise(np.array([[1.0 + 0.5 / 32768, 1.0 + 1.5 / 32768, 7.99999999]]), 8)
+    assert list(fq[0]) == [0, 2, 0] and list(c[0]) == [1, 1, 0]
+
+
+# --- PM force (§2.4 steps 2-4) ---------------------------------------------------------------
+
+def test_zero_self_force_single_particle():
+    nm = 16
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        x = rng.uniform(0, BOX, size=(1, 3))
+        f, _ = pm.pm_accel(x, BOX, nm, nm)
+        assert np.abs(f).max() < 1e-12 * BOX / nm
+
+
+def test_pair_antisymmetry_and_momentum_conservation():
+    nm = 16
+    rng = np.random.default_rng(6)
+    x = rng.uniform(0, BOX, size=(2, 3))
+    f, _ = pm.pm_accel(x, BOX, nm, nm)
+    assert np.abs(f[0] + f[1]).max() < 1e-12 * np.abs(f).max()
+    x = rng.uniform(0, BOX, size=(40, 3))
+    f, _ = pm.pm_accel(x, BOX, nm, nm)
+    assert np.abs(f.sum(axis=0)).max() < 1e-11 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("sep", [5.0, 7.0])
+def test_newtonian_limit_pair(sep):
+    # Far from the mesh scale the pair force approaches -M r_hat / (4 pi r^2), M = (L/N_p)^3 per particle.
+    nm = 64
+    box = float(nm)                       # cell = 1
+    d = np.array([1.0, 0.7, 0.4])
+    d /= np.linalg.norm(d)
+    x = np.array([[20.3, 21.1, 22.7], [0, 0, 0]])
+    x[1] = x[0] + sep * d
+    f, _ = pm.pm_accel(x, box, nm, nm)
+    expect = sep ** -2 / (4 * math.pi) * d            # particle 0 is pulled toward particle 1
+    assert np.linalg.norm(f[0] - expect) < 0.03 * np.linalg.norm(expect)
+
+
+def test_mesh_force_of_a_sinusoid_is_exact():
+    nm, amp = 16, 0.1
+    k1 = 2 * math.pi / BOX
+    xg = np.arange(nm) * BOX / nm
+    delta = np.broadcast_to(amp * np.cos(k1 * xg), (nm, nm, nm)).copy()
+    force = pm.force_mesh(delta, BOX, deconv=0)
+    assert np.abs(force[0] - (-(amp / k1) * np.sin(k1 * xg))).max() < 1e-12 * amp / k1
+    # With deconv = 1 the mode is divided by W(k1) = sinc^2(pi/N).
+    w = (math.sin(math.pi / nm) / (math.pi / nm)) ** 2
+    force1 = pm.force_mesh(delta, BOX, deconv=1)
+    assert np.abs(force1[0] * w - force[0]).max() < 1e-12 * amp / k1
+
+
+# --- COLA / PM stepping (§2.3) -------------------------------------------------------------
+
+def pancake_error(np_, nm, n_steps, cola_on, stepping="modified", amp=0.5):
+    r = cola.Run(BOX, np_, nm, 0.3, 9.0, 0.0, n_steps, stepping=stepping, cola=cola_on)
+    a = amp / r.table["D1"][-1]
+    r.set_displacements(*ics.lpt_displacements(plane_wave_field(np_, [((1, 0, 0), a)]), BOX))
+    if cola_on:
+        assert not r.p.any()                     # residual momentum starts at zero
+    r.run()
+    exact = r.table["D1"][-1] * r.psi1           # x = q + D1 Psi1 before shell crossing
+    return np.sqrt(np.mean((r.displacement() - exact) ** 2)) / np.abs(exact).max()
+
+
+def test_pancake_cola_ten_steps():
+    # 1-D Zel'dovich solution is exact before shell crossing; the remaining error is the PM
+    # discreteness of 32 sheets (measured 9.8e-3 at 32^3, 3.8e-3 at 64^3).
+    assert pancake_error(32, 32, 10, True) < 1.5e-2
+
+
+def test_pancake_plain_pm_converges():
+    # COLA off: the kick normalisation alone must reproduce linear growth (50 steps: 8.8e-3).
+    assert pancake_error(32, 32, 50, False) < 1.5e-2
+    assert pancake_error(32, 32, 50, False, stepping="quinn") < 1.5e-2
+
+
+def test_quinn_and_modified_stepping_converge():
+    pk = cosmology.linear_pk(0.3, 0.7, 0.96, 0.8)
+    out = {}
+    for st in ("quinn", "modified"):
+        r = cola.Run(BOX, 8, 8, 0.3, 9.0, 0.0, 200, stepping=st)
+        r.make_ics(5, pk)
+        r.run()
+        out[st] = r.displacement()
+    scale = np.abs(out["quinn"]).max()
+    assert np.abs(out["quinn"] - out["modified"]).max() < 2e-3 * scale
+
+
+# --- Power spectrum (§7.1) ---------------------------------------------------------------
+
+def test_power_parseval_and_mode_count():
+    n = 12
+    rng = np.random.default_rng(8)
+    delta = rng.standard_normal((n, n, n))
+    dk = fft.fftn(delta)
+    kx, ky, kz, nyq = ics.wavevectors(n, BOX)
+    dk[nyq] = 0                                 # band-limit so every mode falls in a bin
+    dk[0, 0, 0] = 0                             # and remove the mean, which no bin holds
+    delta = fft.ifftn(dk).real
+    kf = 2 * math.pi / BOX
+    kmin, kmax = kf, kf * n                     # above sqrt(3) (n/2 - 1) kf
+    kmean, pb, cnt = power.binned_power(dk, BOX, 10, kmin, kmax, window=False)
+    total = np.nansum(pb * cnt) * n ** 6 / BOX ** 3
+    assert abs(total / (n ** 3 * (delta ** 2).sum()) - 1) < 1e-12      # Parseval
+    # Brute-force mode count over the integer lattice.
+    edges = kmin * (kmax / kmin) ** (np.arange(11) / 10)
+    brute = np.zeros(10, int)
+    s = range(-n // 2 + 1, n // 2)
+    for i, j, k in itertools.product(s, s, s):
+        km = kf * math.sqrt(i * i + j * j + k * k)
+        for b in range(10):
+            if edges[b] <= km < edges[b + 1]:
+                brute[b] += 1
+    assert np.array_equal(cnt, brute)
+
+
+def test_power_single_mode_and_cross_correlation():
+    n = 16
+    dk = plane_wave_field(n, [((2, 1, 0), 0.1)])
+    kf = 2 * math.pi / BOX
+    kmean, pb, cnt = power.binned_power(dk, BOX, 20, kf, kf * n / 2, window=False)
+    b = np.flatnonzero(np.nan_to_num(pb) > 0)
+    assert len(b) == 1
+    # Two modes (+-k) of |delta_k|^2 = (0.1 N^3 / 2)^2 each: P = L^3 0.01 / 4 per mode.
+    assert abs(pb[b[0]] * cnt[b[0]] / 2 / (BOX ** 3 * 0.01 / 4) - 1) < 1e-12
+    r = power.cross_correlation(dk, 3.0 * dk, BOX, 20, kf, kf * n / 2)
+    assert abs(r[b[0]] - 1) < 1e-12
+    r = power.cross_correlation(dk, -dk, BOX, 20, kf, kf * n / 2)
+    assert abs(r[b[0]] + 1) < 1e-12
