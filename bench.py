@@ -1,0 +1,310 @@
+"""Benchmark of the COLA particle-mesh hot path on GB300.
+
+One bench step = one whole mock realisation of the 512^3-particle / 1024^3-mesh / 1024 Mpc/h
+workload: 2LPT initial conditions from a new seed, 10 COLA steps (deposit, FFT Poisson solve
+with gradient and CIC deconvolution, inverse FFTs, gather + kick + drift) and the 100-bin
+power spectrum. The metric is particle-updates per second (N_p^3 x 10 per step / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+With --gpus N > 1 (launched by torchrun) every rank runs independent mocks (replicas, no
+data-path collective); the time is the max over ranks. The reference arm times the FP64
+CPU oracle on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1506_03737_gb300 import workloads  # noqa: E402
+
+# Algorithmic bytes (minimum HBM traffic) per COLA step, per the layout in the design doc:
+# particles 96 B per particle-update; mesh 80 B per cell.
+ALG_BYTES_PARTICLE = 96
+ALG_BYTES_CELL = 80
+# Per-kernel algorithmic bytes per cell (mesh kernels) or particle (particle kernels).
+ALG_PHASE = {
+    "poisson": ("cell", 16),     # z pass: read the half spectrum once, write three force spectra
+    "fft_inv": ("cell", 24),     # inverse passes: read three spectra, write three real meshes
+    "fft_fwd": ("cell", 12),     # forward passes: read int64 density, write half spectrum
+    "deposit": ("cell", 16),     # zero + atomic write-back of the int64 mesh (+16 B/particle below)
+    "gather": ("particle", 80),  # read pos, mom, psi1, psi2, write pos, mom (+12 B/cell below)
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cola_512p_1024m_1024mpc")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and "Active" == r[3 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# --- CPU side: the oracle ---------------------------------------------------------------------
+
+def oracle_sample(seed=1):
+    """One oracle mock on a bounded sub-volume of the workload: 32^3 particles on a 64^3 mesh in a
+    64 Mpc/h box (same 2 Mpc/h particle spacing and N_m = 2 N_p as the 512^3 / 1024 Mpc/h case),
+    2LPT at z = 9, 10 COLA steps, 100-bin P(k). Returns (particle-updates, seconds)."""
+    from oracle import cola, cosmology, power
+    kw = workloads.COSMO
+    t0 = time.perf_counter()
+    r = cola.Run(64.0, 32, 64, kw["omega_m"], 9.0, 0.0, 10)
+    r.make_ics(seed, cosmology.linear_pk(kw["omega_m"], kw["h"], kw["n_s"], kw["sigma8"]))
+    r.run()
+    power.power_from_positions(r.x, 64.0, 32, 64, 100)
+    return 32 ** 3 * 10, time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s=20.0):
+    ups, secs, n = 0, 0.0, 0
+    while secs < budget_s or n == 0:
+        u, s = oracle_sample(seed=1000 + n)
+        ups += u
+        secs += s
+        n += 1
+        if n >= 4:
+            break
+    return {"value": ups / secs, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle mocks of 32^3 particles / 64^3 mesh / 64 Mpc/h (2LPT, 10 COLA steps, "
+                      f"P(k)); same particle spacing and mesh ratio as the 512^3 / 1024^3 workload; "
+                      f"single-threaded numpy FP64, {secs:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(seed=7)
+    ups, secs = 0, 0.0
+    for i in range(args.steps):
+        u, s = oracle_sample(seed=100 + i)
+        ups += u
+        secs += s
+    v = ups / secs
+    line = {"impl": "reference", "metric": "particle-updates/s per COLA step", "value": v,
+            "unit": "particle-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": "32^3 particles / 64^3 mesh / 64 Mpc/h sub-volume"},
+            "cpu_baseline": {"value": v, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} oracle mocks of 32^3 / 64^3 / 64 Mpc/h"},
+            "e2e": {"value": v, "unit": "particle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --- GPU side ---------------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_1506_03737_gb300 import colapm as C
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    kw = workloads.run_params(args.workload)
+    np_, nm, nsteps = kw["np"], kw["nm"], kw["n_steps"]
+    stream = torch.cuda.Stream()
+    ctx = C.colapm_create(C.default_params(**kw), stream.cuda_stream)
+    nbins = 100
+    kd = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    pd = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    nd = torch.empty(nbins, dtype=torch.int64, device="cuda")
+
+    def mock(seed, k_out, p_out, n_out):
+        C.colapm_reseed(ctx, seed)
+        C.colapm_make_ics(ctx)
+        C.colapm_step(ctx, -1)
+        C.colapm_power(ctx, nbins, 0.0, 0.0, k_out, p_out, n_out)
+
+    seed0 = 1000 * (rank + 1)
+    for w in range(args.warmup):
+        mock(seed0 + w, kd, pd, nd)
+    C.colapm_get_timing(ctx)                     # clear
+    C.colapm_set_timing(ctx, True)
+    launches0 = C.colapm_kernel_launches(ctx)
+
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for s in range(args.steps):
+            mock(seed0 + 100 + s, kd, pd, nd)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms)
+    launches = C.colapm_kernel_launches(ctx) - launches0
+    phase_ms, phase_n = C.colapm_get_timing(ctx)
+    C.colapm_set_timing(ctx, False)
+
+    updates = np_ ** 3 * nsteps * args.steps * world
+    value = updates / (ms_max / 1e3)
+
+    # end to end: host buffers through the public C calls, the step's result read back to host
+    e2e = None
+    if not args.no_e2e:
+        kh = torch.empty(nbins, dtype=torch.float64, pin_memory=True)
+        ph = torch.empty(nbins, dtype=torch.float64, pin_memory=True)
+        nh = torch.empty(nbins, dtype=torch.int64, pin_memory=True)
+        posh = torch.empty((np_ ** 3, 3), dtype=torch.float32, pin_memory=True)
+        momh = torch.empty((np_ ** 3, 3), dtype=torch.float32, pin_memory=True)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            mock(seed0 + 200 + s, kh, ph, nh)
+            C.colapm_get_particles(ctx, posh, momh)
+        torch.cuda.synchronize()
+        barrier()
+        secs = max_over_ranks(time.perf_counter() - t0)
+        d2h = nbins * 24 + posh.numel() * 4 + momh.numel() * 4
+        e2e = {"value": updates / secs, "unit": "particle-updates/s", "h2d_bytes_per_step": 8,
+               "d2h_bytes_per_step": d2h,
+               "note": "inputs are the seed and parameters (8 B per mock); outputs are P(k) and the final "
+                       "particle catalogue (positions and momenta, float32 xyz) copied to pinned host memory"}
+
+    # roofline of the dominant kernel: the phase with the largest share that is one kernel
+    hbm, peak_src = peaks()
+    per_call = {}
+    for name, (unit, b) in ALG_PHASE.items():
+        n = max(int(phase_n[name]), 1)
+        per_call[name] = phase_ms[name] / n
+    single = ["poisson", "gather"]
+    dom = max(single, key=lambda k: phase_ms[k])
+    unit, b = ALG_PHASE[dom]
+    nbytes = b * (nm ** 3 if unit == "cell" else np_ ** 3)
+    if dom == "gather":
+        nbytes += 12 * nm ** 3
+    achieved = nbytes / (per_call[dom] / 1e3) / 1e9
+    alg_step = ALG_BYTES_PARTICLE * np_ ** 3 + ALG_BYTES_CELL * nm ** 3
+
+    line = {
+        "metric": "particle-updates/s per COLA step", "value": value, "unit": "particle-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "np": np_, "nm": nm, "box_mpc_h": kw["box"], "cola_steps": nsteps,
+                   "step": "2LPT ICs + 10 COLA steps + 100-bin P(k), new seed each step",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (particle state and meshes ~35 GB)"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs"},
+        "cola_step_ms": sum(phase_ms[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "gather"))
+                        / max(int(phase_n["gather"]), 1),
+        "cola_step_roofline_frac": None,
+        "phase_ms_per_mock": {k: v / args.steps for k, v in phase_ms.items()},
+        "clocks": clk.summary(),
+    }
+    step_ms = line["cola_step_ms"]
+    line["cola_step_roofline_frac"] = alg_step / (step_ms / 1e3) / 1e9 / hbm
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    C.colapm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

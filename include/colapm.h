@@ -1,0 +1,192 @@
+/*
+ * colapm.h -- C ABI of libcolapm.so, a single-GPU (GB300, sm_103a) implementation of the
+ * COLA particle-mesh method of Howlett, Manera & Percival, "L-PICOLA: A parallel code for
+ * fast dark matter simulation" (2015).
+ *
+ * The calls follow the paper's statement of the problem (§3): prepare the initial linear
+ * power spectrum, generate an initial particle distribution with that power spectrum,
+ * evolve it over a series of user-specified timesteps to a final redshift, and measure
+ * the result.
+ *
+ * Conventions for every call:
+ *   - Return COLAPM_OK (0) or a negative COLAPM_E_* code; nothing throws across the ABI.
+ *   - A context owns all of its device memory. Arrays passed in are owned by the caller.
+ *   - "host or device" arrays may be either (CUDA unified addressing decides); the call
+ *     copies with cudaMemcpyAsync on the context's stream.
+ *   - Work is issued on the stream given to colapm_create (0 = the legacy default
+ *     stream). Calls return before the GPU finishes unless they write host data or say
+ *     otherwise; a device-side error (e.g. fixed-point overflow) is reported by the next
+ *     call that synchronises (colapm_sync, colapm_power, colapm_get_*).
+ *   - Units: lengths in Mpc/h, wavenumbers in h/Mpc, time in 1/H0 (H0 = 1). Momenta are
+ *     p = a^3 E(a) dx/da in Mpc/h (peculiar velocity in km/s = 100 p / a).
+ *   - Particle arrays are in particle-id order, id = ix + Np (iy + Np iz), where
+ *     (ix, iy, iz) is the particle's site on the Lagrangian lattice; xyz-interleaved
+ *     ("xyz") arrays hold 3 values per particle, component-major ("c-major") arrays hold
+ *     all x, then all y, then all z.
+ *   - Meshes are [iz][iy][ix] with ix fastest.
+ */
+#ifndef COLAPM_H
+#define COLAPM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    COLAPM_OK = 0,
+    COLAPM_E_ARG = -1,      /* invalid argument: null pointer, size out of range, bad enum      */
+    COLAPM_E_NOMEM = -2,    /* device or host allocation failed                                 */
+    COLAPM_E_CUDA = -3,     /* a CUDA runtime call or kernel launch failed                      */
+    COLAPM_E_OVERFLOW = -4, /* a density cell reached 2^63 in the int64 fixed-point deposit     */
+    COLAPM_E_TIMEOUT = -5,  /* a bounded device-side wait gave up                               */
+    COLAPM_E_STATE = -6     /* call out of order (e.g. colapm_step before initial conditions)   */
+};
+
+/* Flat LCDM cosmology, Omega_Lambda = 1 - omega_m. omega_b is carried for completeness; the
+ * BBKS transfer function uses Gamma = omega_m * h. sigma8 normalises P(k) at z = 0. */
+typedef struct {
+    double omega_m, omega_b, h, n_s, sigma8;
+} colapm_cosmo;
+
+/* Run parameters (§2.3, §2.4, §5, §7.3). */
+typedef struct {
+    colapm_cosmo cosmo;
+    double box;                 /* box side L, Mpc/h                                            */
+    int np;                     /* particles per side N_p (even, 8..1024)                       */
+    int nm;                     /* PM mesh cells per side N_m (even, 8..1024, a multiple of N_p)*/
+    double z_init, z_final;     /* redshift of the 2LPT initial conditions and of the last step */
+    int n_steps;                /* number of Kick-Drift steps (§2.3)                             */
+    int spacing;                /* 0: steps linear in a (default), 1: logarithmic in a (§7.3)   */
+    int stepping;               /* 0: modified COLA stepping, Eq. eq:modifiedt (default);        */
+                                /* 1: Quinn et al. (1997) stepping (§2.3)                        */
+    double nlpt;                /* n of the modified stepping (default -2.5, §1 and §7.3)       */
+    int cola;                   /* 1: COLA (default); 0: plain PM (§7.1)                         */
+    int deconv;                 /* powers of the CIC window divided out of the force: 0, 1, 2   */
+    unsigned long long seed;    /* Philox4x32-10 key of the Gaussian field                      */
+} colapm_params;
+
+typedef struct colapm_ctx colapm_ctx;   /* opaque; owns all device memory */
+
+/* Fill *p with the defaults above: omega_m 0.3, omega_b 0.05, h 0.7, n_s 0.96, sigma8 0.8,
+ * box 256, np 32, nm 64, z_init 9, z_final 0, 10 steps, lin-a, modified, nlpt -2.5, COLA,
+ * deconv 1, seed 1. */
+void colapm_default_params(colapm_params* p);
+
+/* Create a context on the current CUDA device: validates *p (COLAPM_E_ARG), computes the FP64
+ * timestep table and the linear P(k) normalisation on the host, allocates every device buffer
+ * (COLAPM_E_NOMEM). `stream` is a cudaStream_t (may be NULL). On success *out owns the memory
+ * until colapm_destroy. */
+int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out);
+
+/* Synchronise the context's stream and free everything. NULL is allowed. */
+void colapm_destroy(colapm_ctx* ctx);
+
+/* §5, §2.1: Gaussian field from Philox4x32-10 (Salmon et al. 2011) keyed by the seed, with
+ * BBKS P(k) at z = 0; 1LPT and 2LPT displacements Psi1 = i k delta/k^2 and Psi2 = -i k S/k^2,
+ * S = sum_{i>j}(phi_ii phi_jj - phi_ij^2) (Eqs. za, 2lpt and the Lagrangian-potential Poisson
+ * equations); particles at x = q + D1(a0) Psi1 + D2(a0) Psi2 on a lattice offset by half a PM
+ * cell; residual momentum 0 (COLA, §2.3) or the 2LPT momentum (plain PM). Resets the step
+ * counter. */
+int colapm_make_ics(colapm_ctx* ctx);
+
+/* Set the seed of the next colapm_make_ics (a new mock realisation from the same context,
+ * without reallocating). */
+int colapm_reseed(colapm_ctx* ctx, unsigned long long seed);
+
+/* Replace the LPT displacements with caller-supplied fields on the N_p^3 Lagrangian lattice
+ * (c-major, 3 * Np^3 floats each, Mpc/h, host or device) and place the particles as
+ * colapm_make_ics does. Used to start from a known field (parity tests, planted modes). */
+int colapm_set_displacements(colapm_ctx* ctx, const float* psi1, const float* psi2);
+
+/* §2.3-§2.4: advance k Kick-Drift steps (k < 0: all remaining). One step at a_i: fixed-point
+ * CIC deposit, FFT, Poisson/gradient/deconvolution, inverse FFT x3, CIC gather, COLA kick
+ * (Eq. eq:vcola) and drift (Eq. eq:rcola). COLAPM_E_STATE before initial conditions or when
+ * k exceeds the remaining steps. */
+int colapm_step(colapm_ctx* ctx, int k);
+
+/* §2.3: closing half kick to a_N (force at a_N), then add the LPT momentum back (COLA).
+ * Allowed once, after the last step; afterwards colapm_get_particles returns total momenta. */
+int colapm_finalize(colapm_ctx* ctx);
+
+/* §7.1: periodic-box power spectrum of the current particles: fixed-point CIC deposit, FFT,
+ * P = L^3 |delta_k|^2 / (N_m^6 W^2), W = prod sinc^2(pi n_i / N_m), binned in nbins log bins
+ * with edges kmin (kmax/kmin)^(b/nbins); a mode is in bin b when e_b <= |k| < e_{b+1}; modes
+ * counted over the full complex grid; k = 0 and modes with any index at N_m/2 excluded. FP64
+ * sums. Outputs (caller-owned, host or device, nbins each): mean |k|, mean P, mode count.
+ * kmin <= 0 selects 2 pi / L, kmax <= 0 selects pi N_m / L. Synchronises. */
+int colapm_power(colapm_ctx* ctx, int nbins, double kmin, double kmax,
+                 double* k_out, double* p_out, long long* nmodes_out);
+
+/* Positions (xyz, Mpc/h, in [0, L)) and momenta (xyz, Mpc/h) of all particles; either pointer
+ * may be NULL. Host or device. Synchronises. */
+int colapm_get_particles(colapm_ctx* ctx, float* pos, float* mom);
+
+/* Raw particle state: integer mesh cell (xyz int32), offset in [0,1) cells (xyz float) and
+ * momentum in mesh units (xyz float, Mpc/h divided by the cell size). Any pointer may be NULL.
+ * Host or device. Synchronises. */
+int colapm_get_state(colapm_ctx* ctx, int* cell, float* offset, float* mom_cells);
+
+/* Overwrite positions with integer cells (xyz int32, each in [0, Nm)) and offsets (xyz float,
+ * each in [0, 1)); COLAPM_E_ARG if any is out of range (checked on the device, reported by
+ * this call, which synchronises). Host or device. */
+int colapm_set_state(colapm_ctx* ctx, const int* cell, const float* offset, const float* mom_cells);
+
+/* Deposit the current particles and copy the int64 fixed-point density (Nm^3, weight of one
+ * particle = 2^45) to `mesh` (host or device). Synchronises. */
+int colapm_get_density(colapm_ctx* ctx, long long* mesh);
+
+/* Compute the mesh force of the current particles (§2.4 steps 1-3, mesh units: cells) and copy
+ * the three real meshes (c-major, 3 * Nm^3 floats) to `force`, host or device. Synchronises. */
+int colapm_get_force(colapm_ctx* ctx, float* force);
+
+/* Copy the LPT displacement fields (c-major, 3 * Np^3 floats each, Mpc/h) to psi1 / psi2
+ * (either may be NULL). Synchronises. */
+int colapm_get_lpt(colapm_ctx* ctx, float* psi1, float* psi2);
+
+/* Copy the initial Gaussian field on the half grid [iz][iy][ix], ix < Np/2, as interleaved
+ * (re, im) floats (Np * Np * Np/2 complex) to `dk`, host or device. Synchronises. */
+int colapm_get_gaussian_field(colapm_ctx* ctx, float* dk);
+
+/* Wait for the context's stream and report any pending device-side error. */
+int colapm_sync(colapm_ctx* ctx);
+
+/* Number of steps taken so far, and the total. */
+int colapm_steps_done(const colapm_ctx* ctx);
+
+/* Checkpoint / resume of the particle state, step counter and LPT fields: with buf == NULL,
+ * *n receives the byte size; otherwise *n must be at least that size and buf (host) receives
+ * the state. colapm_load_state restores a buffer written by a context with the same np, nm.
+ * Both synchronise. */
+int colapm_save_state(colapm_ctx* ctx, void* buf, size_t* n);
+int colapm_load_state(colapm_ctx* ctx, const void* buf, size_t n);
+
+/* Per-phase device timing with CUDA events (off by default). When on, each phase of every
+ * call is bracketed by events on the context's stream. colapm_get_timing copies, for each
+ * of the COLAPM_PHASE_COUNT phases, the summed milliseconds and the launch count, then
+ * clears them (synchronises). */
+enum {
+    COLAPM_PHASE_DEPOSIT = 0,   /* zero + fixed-point CIC deposit                   */
+    COLAPM_PHASE_FFT_FWD,       /* x and y forward passes of the density            */
+    COLAPM_PHASE_POISSON,       /* z forward, Green/gradient/deconvolution, z inverse */
+    COLAPM_PHASE_FFT_INV,       /* y and x inverse passes of the three forces       */
+    COLAPM_PHASE_GATHER,        /* CIC gather + kick + drift                        */
+    COLAPM_PHASE_ICS,           /* initial conditions                               */
+    COLAPM_PHASE_POWER,         /* power-spectrum transform and binning             */
+    COLAPM_PHASE_COUNT
+};
+int colapm_set_timing(colapm_ctx* ctx, int on);
+int colapm_get_timing(colapm_ctx* ctx, double* ms, long long* launches);
+
+/* Number of CUDA kernels this context has launched so far (memsets and copies excluded). */
+long long colapm_kernel_launches(const colapm_ctx* ctx);
+
+/* Static message for an error code. */
+const char* colapm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COLAPM_H */

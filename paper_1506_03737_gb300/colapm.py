@@ -1,0 +1,218 @@
+"""Thin ctypes binding of libcolapm.so (argument marshalling only).
+
+The functions carry the C names of ``include/colapm.h``. Array arguments may be numpy
+arrays (host) or torch tensors (host or CUDA); they must be C-contiguous with the dtype
+the C call expects. Every call raises ``ColapmError`` on a non-zero return code.
+There is no CPU fallback: importing this module fails when the library is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libcolapm.so")
+
+PHASES = ["deposit", "fft_fwd", "poisson", "fft_inv", "gather", "ics", "power"]
+
+
+class ColapmError(RuntimeError):
+    def __init__(self, code, call):
+        super().__init__(f"{call} failed: {code} ({strerror(code)})")
+        self.code = code
+
+
+class Cosmo(ctypes.Structure):
+    _fields_ = [("omega_m", ctypes.c_double), ("omega_b", ctypes.c_double), ("h", ctypes.c_double),
+                ("n_s", ctypes.c_double), ("sigma8", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("cosmo", Cosmo), ("box", ctypes.c_double), ("np", ctypes.c_int), ("nm", ctypes.c_int),
+                ("z_init", ctypes.c_double), ("z_final", ctypes.c_double), ("n_steps", ctypes.c_int),
+                ("spacing", ctypes.c_int), ("stepping", ctypes.c_int), ("nlpt", ctypes.c_double),
+                ("cola", ctypes.c_int), ("deconv", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libcolapm.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, I, D, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "colapm_default_params": (None, [ctypes.POINTER(Params)]),
+        "colapm_create": (I, [ctypes.POINTER(Params), P, ctypes.POINTER(P)]),
+        "colapm_destroy": (None, [P]),
+        "colapm_make_ics": (I, [P]),
+        "colapm_set_displacements": (I, [P, P, P]),
+        "colapm_step": (I, [P, I]),
+        "colapm_finalize": (I, [P]),
+        "colapm_power": (I, [P, I, D, D, P, P, P]),
+        "colapm_get_particles": (I, [P, P, P]),
+        "colapm_get_state": (I, [P, P, P, P]),
+        "colapm_set_state": (I, [P, P, P, P]),
+        "colapm_get_density": (I, [P, P]),
+        "colapm_get_force": (I, [P, P]),
+        "colapm_get_lpt": (I, [P, P, P]),
+        "colapm_get_gaussian_field": (I, [P, P]),
+        "colapm_sync": (I, [P]),
+        "colapm_reseed": (I, [P, ctypes.c_ulonglong]),
+        "colapm_kernel_launches": (ctypes.c_longlong, [P]),
+        "colapm_steps_done": (I, [P]),
+        "colapm_save_state": (I, [P, P, ctypes.POINTER(Z)]),
+        "colapm_load_state": (I, [P, P, Z]),
+        "colapm_set_timing": (I, [P, I]),
+        "colapm_get_timing": (I, [P, P, P]),
+        "colapm_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+EXPORTED = [n for n in dir(LIB) if n.startswith("colapm_")]
+
+
+def strerror(code):
+    return LIB.colapm_strerror(code).decode()
+
+
+def _check(code, call):
+    if code != 0:
+        raise ColapmError(code, call)
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def default_params(**kw):
+    p = Params()
+    LIB.colapm_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("omega_m", "omega_b", "h", "n_s", "sigma8"):
+            setattr(p.cosmo, k, v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def colapm_create(params, stream=0):
+    ctx = ctypes.c_void_p()
+    _check(LIB.colapm_create(ctypes.byref(params), ctypes.c_void_p(stream or None), ctypes.byref(ctx)),
+           "colapm_create")
+    return ctx
+
+
+def colapm_destroy(ctx):
+    LIB.colapm_destroy(ctx)
+
+
+def colapm_make_ics(ctx):
+    _check(LIB.colapm_make_ics(ctx), "colapm_make_ics")
+
+
+def colapm_set_displacements(ctx, psi1, psi2):
+    _check(LIB.colapm_set_displacements(ctx, _ptr(psi1), _ptr(psi2)), "colapm_set_displacements")
+
+
+def colapm_step(ctx, k=-1):
+    _check(LIB.colapm_step(ctx, k), "colapm_step")
+
+
+def colapm_finalize(ctx):
+    _check(LIB.colapm_finalize(ctx), "colapm_finalize")
+
+
+def colapm_power(ctx, nbins, kmin=0.0, kmax=0.0, k_out=None, p_out=None, n_out=None):
+    k_out = np.empty(nbins) if k_out is None else k_out
+    p_out = np.empty(nbins) if p_out is None else p_out
+    n_out = np.empty(nbins, dtype=np.int64) if n_out is None else n_out
+    _check(LIB.colapm_power(ctx, nbins, kmin, kmax, _ptr(k_out), _ptr(p_out), _ptr(n_out)), "colapm_power")
+    return k_out, p_out, n_out
+
+
+def colapm_get_particles(ctx, pos=None, mom=None):
+    _check(LIB.colapm_get_particles(ctx, _ptr(pos), _ptr(mom)), "colapm_get_particles")
+    return pos, mom
+
+
+def colapm_get_state(ctx, cell=None, offset=None, mom=None):
+    _check(LIB.colapm_get_state(ctx, _ptr(cell), _ptr(offset), _ptr(mom)), "colapm_get_state")
+    return cell, offset, mom
+
+
+def colapm_set_state(ctx, cell=None, offset=None, mom=None):
+    _check(LIB.colapm_set_state(ctx, _ptr(cell), _ptr(offset), _ptr(mom)), "colapm_set_state")
+
+
+def colapm_get_density(ctx, mesh):
+    _check(LIB.colapm_get_density(ctx, _ptr(mesh)), "colapm_get_density")
+    return mesh
+
+
+def colapm_get_force(ctx, force):
+    _check(LIB.colapm_get_force(ctx, _ptr(force)), "colapm_get_force")
+    return force
+
+
+def colapm_get_lpt(ctx, psi1=None, psi2=None):
+    _check(LIB.colapm_get_lpt(ctx, _ptr(psi1), _ptr(psi2)), "colapm_get_lpt")
+    return psi1, psi2
+
+
+def colapm_get_gaussian_field(ctx, dk):
+    _check(LIB.colapm_get_gaussian_field(ctx, _ptr(dk)), "colapm_get_gaussian_field")
+    return dk
+
+
+def colapm_reseed(ctx, seed):
+    _check(LIB.colapm_reseed(ctx, seed), "colapm_reseed")
+
+
+def colapm_kernel_launches(ctx):
+    return LIB.colapm_kernel_launches(ctx)
+
+
+def colapm_sync(ctx):
+    _check(LIB.colapm_sync(ctx), "colapm_sync")
+
+
+def colapm_steps_done(ctx):
+    return LIB.colapm_steps_done(ctx)
+
+
+def colapm_save_state(ctx):
+    n = ctypes.c_size_t(0)
+    _check(LIB.colapm_save_state(ctx, None, ctypes.byref(n)), "colapm_save_state")
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(LIB.colapm_save_state(ctx, _ptr(buf), ctypes.byref(n)), "colapm_save_state")
+    return buf
+
+
+def colapm_load_state(ctx, buf):
+    _check(LIB.colapm_load_state(ctx, _ptr(buf), buf.nbytes), "colapm_load_state")
+
+
+def colapm_set_timing(ctx, on=True):
+    _check(LIB.colapm_set_timing(ctx, 1 if on else 0), "colapm_set_timing")
+
+
+def colapm_get_timing(ctx):
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
+    _check(LIB.colapm_get_timing(ctx, _ptr(ms), _ptr(cnt)), "colapm_get_timing")
+    return dict(zip(PHASES, ms)), dict(zip(PHASES, cnt))

@@ -1,0 +1,672 @@
+// C ABI of libcolapm.so (declared in include/colapm.h): context, initial conditions, the
+// COLA / PM step loop, finalisation, power spectrum, state I/O and phase timing.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "colapm_internal.h"
+#include "cosmology.h"
+
+using namespace colapm;
+
+struct colapm_ctx {
+    colapm_params prm{};
+    cudaStream_t stream = nullptr;
+    int np = 0, nm = 0;
+    size_t np3 = 0, nm3 = 0;
+    StepTable table;
+    // device buffers
+    unsigned long long* rho = nullptr;   // nm^3 int64 fixed-point density
+    float* F = nullptr;                  // 3 nm^3: density spectrum, then the three force meshes
+    float4* pos = nullptr;               // np^3 (offsets, cell bits)
+    float* mom = nullptr;                // 3 np^3, cells
+    float* psi1 = nullptr;               // 3 np^3, cells
+    float* psi2 = nullptr;               // 3 np^3, cells
+    float* scratch = nullptr;            // 9 np^3 (IC spectra and phi_ij; staging for state I/O)
+    float2* tw_m = nullptr;              // exp(-2 pi i t / nm)
+    float2* tw_p = nullptr;              // exp(-2 pi i t / np)
+    float* sinc2_m = nullptr;            // sinc^2(pi n / nm) per FFT bin
+    float* amp_p = nullptr;              // Gaussian-field amplitude per integer |n|^2 of the IC grid
+    int* err = nullptr;                  // device error bits: 1 overflow, 2 bad state import
+    // power-spectrum tables (grown on demand)
+    int* pw_bin = nullptr;
+    double* pw_kmag = nullptr;
+    double* pw_acc = nullptr;            // ksum[nb], psum[nb], cnt[nb] (as u64)
+    int pw_n2cap = 0, pw_nbcap = 0;
+    int step = 0;
+    long long launches = 0;              // kernels launched by this context
+    bool has_ics = false, finalized = false;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[COLAPM_PHASE_COUNT];
+};
+
+namespace {
+
+constexpr int kMeshSizes[] = {16, 32, 64, 96, 128, 160, 192, 256, 320, 384, 512, 1024};
+
+bool supported_size(int n) {
+    for (int s : kMeshSizes)
+        if (s == n) return true;
+    return false;
+}
+
+#define CK(call)                                \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return COLAPM_E_CUDA; \
+    } while (0)
+
+#define CKL(call)                               \
+    do {                                        \
+        ++c->launches;                          \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return COLAPM_E_CUDA; \
+    } while (0)
+
+struct Phase {   // CUDA-event bracket of one phase when timing is on
+    colapm_ctx* c;
+    int ph;
+    cudaEvent_t b = nullptr, e = nullptr;
+    Phase(colapm_ctx* ctx, int phase) : c(ctx), ph(phase) {
+        if (!c->timing) return;
+        if (cudaEventCreate(&b) == cudaSuccess && cudaEventCreate(&e) == cudaSuccess) cudaEventRecord(b, c->stream);
+    }
+    ~Phase() {
+        if (!c->timing || !b || !e) return;
+        cudaEventRecord(e, c->stream);
+        c->ev[ph].emplace_back(b, e);
+    }
+};
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_all(colapm_ctx* c) {
+    void* ptrs[] = {c->rho, c->F, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
+                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_kmag, c->pw_acc};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& v : c->ev)
+        for (auto& pr : v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+}
+
+std::vector<float2> twiddles(int n) {
+    std::vector<float2> t(n);
+    for (int i = 0; i < n; ++i) {
+        const double ang = 2.0 * M_PI * (double)i / n;
+        t[i] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    return t;
+}
+
+int pending_error(colapm_ctx* c) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h) CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    if (h & 1) return COLAPM_E_OVERFLOW;
+    if (h & 2) return COLAPM_E_ARG;
+    return COLAPM_OK;
+}
+
+// Copy `bytes` produced on the device (src) to a caller array that may be host or device.
+int copy_out(colapm_ctx* c, void* dst, const void* src, size_t bytes) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    return COLAPM_OK;
+}
+
+int deposit(colapm_ctx* c) {
+    Phase ph(c, COLAPM_PHASE_DEPOSIT);
+    CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
+    CKL(launch_deposit(c->pos, c->np3, c->nm, c->rho, c->stream));
+    return COLAPM_OK;
+}
+
+float density_scale(const colapm_ctx* c) {
+    const double m = (double)c->nm / c->np;
+    return (float)(m * m * m * std::ldexp(1.0, -45));
+}
+
+// Forward x and y passes of the current density into F (half spectrum, z still in real space).
+int density_xy(colapm_ctx* c) {
+    Phase ph(c, COLAPM_PHASE_FFT_FWD);
+    float2* d = reinterpret_cast<float2*>(c->F);
+    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream));
+    CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream));
+    return COLAPM_OK;
+}
+
+// §2.4 steps 1-3: the three real force meshes F_j = -d psi / dx_j (cells) in c->F.
+int compute_force(colapm_ctx* c) {
+    int r = deposit(c);
+    if (r) return r;
+    r = density_xy(c);
+    if (r) return r;
+    float2* d = reinterpret_cast<float2*>(c->F);
+    const size_t fs = c->nm3 / 2;   // complex stride between the three meshes
+    {
+        Phase ph(c, COLAPM_PHASE_POISSON);
+        ZOut out{};
+        out.p[0] = d;
+        out.p[1] = d + fs;
+        out.p[2] = d + 2 * fs;
+        const float gnorm = (float)(1.0 / ((double)c->nm * c->nm * c->nm));
+        CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream));
+    }
+    {
+        Phase ph(c, COLAPM_PHASE_FFT_INV);
+        CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream));
+        CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream));
+    }
+    return COLAPM_OK;
+}
+
+StepCoef coef_for(const colapm_ctx* c, int i) {
+    const StepTable& t = c->table;
+    StepCoef k{};
+    k.kick = (float)t.kick[i];
+    k.drift = (float)t.drift[i];
+    if (c->prm.cola) {
+        k.c1 = (float)t.g[i].d1;
+        k.c2 = (float)(t.g[i].d2 - t.g[i].d1 * t.g[i].d1);
+        k.e1 = (float)(t.g[i + 1].d1 - t.g[i].d1);
+        k.e2 = (float)(t.g[i + 1].d2 - t.g[i].d2);
+    }
+    return k;
+}
+
+// Particles from the LPT fields in psi1/psi2 (units: to_mesh converts them to mesh cells).
+int place_particles(colapm_ctx* c, float to_mesh) {
+    const Growth& g = c->table.g[0];
+    CKL(launch_init_particles(c->pos, c->mom, c->psi1, c->psi2, c->np, c->nm, to_mesh, (float)g.d1, (float)g.d2,
+                             (float)g.p1, (float)g.p2, c->prm.cola, c->stream));
+    c->step = 0;
+    c->has_ics = true;
+    c->finalized = false;
+    return COLAPM_OK;
+}
+
+int validate(const colapm_params* p) {
+    if (!p) return COLAPM_E_ARG;
+    if (!supported_size(p->np) || !supported_size(p->nm) || p->nm % p->np != 0) return COLAPM_E_ARG;
+    if (!(p->box > 0) || !(p->cosmo.omega_m > 0 && p->cosmo.omega_m <= 1) || !(p->cosmo.h > 0) ||
+        !(p->cosmo.sigma8 > 0))
+        return COLAPM_E_ARG;
+    if (!(p->z_init > p->z_final) || !(p->z_final >= 0) || p->n_steps < 1 || p->n_steps > 100000) return COLAPM_E_ARG;
+    if (p->spacing < 0 || p->spacing > 1 || p->stepping < 0 || p->stepping > 1) return COLAPM_E_ARG;
+    if (p->stepping == 0 && p->nlpt == 0.0) return COLAPM_E_ARG;
+    if (p->deconv < 0 || p->deconv > 2 || (p->cola != 0 && p->cola != 1)) return COLAPM_E_ARG;
+    return COLAPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void colapm_default_params(colapm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->cosmo.omega_m = 0.3;
+    p->cosmo.omega_b = 0.05;
+    p->cosmo.h = 0.7;
+    p->cosmo.n_s = 0.96;
+    p->cosmo.sigma8 = 0.8;
+    p->box = 256.0;
+    p->np = 32;
+    p->nm = 64;
+    p->z_init = 9.0;
+    p->z_final = 0.0;
+    p->n_steps = 10;
+    p->spacing = 0;
+    p->stepping = 0;
+    p->nlpt = -2.5;
+    p->cola = 1;
+    p->deconv = 1;
+    p->seed = 1;
+}
+
+const char* colapm_strerror(int code) {
+    switch (code) {
+        case COLAPM_OK: return "ok";
+        case COLAPM_E_ARG: return "invalid argument";
+        case COLAPM_E_NOMEM: return "out of memory";
+        case COLAPM_E_CUDA: return "CUDA error";
+        case COLAPM_E_OVERFLOW: return "fixed-point density overflow";
+        case COLAPM_E_TIMEOUT: return "device wait timed out";
+        case COLAPM_E_STATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
+    if (!out) return COLAPM_E_ARG;
+    *out = nullptr;
+    int r = validate(p);
+    if (r) return r;
+    colapm_ctx* c = new (std::nothrow) colapm_ctx();
+    if (!c) return COLAPM_E_NOMEM;
+    c->prm = *p;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->np = p->np;
+    c->nm = p->nm;
+    c->np3 = (size_t)p->np * p->np * p->np;
+    c->nm3 = (size_t)p->nm * p->nm * p->nm;
+    c->table = make_step_table(p->cosmo.omega_m, p->z_init, p->z_final, p->n_steps, p->spacing, p->stepping, p->nlpt);
+
+    bool ok = dalloc(&c->rho, c->nm3) == cudaSuccess && dalloc(&c->F, 3 * c->nm3) == cudaSuccess &&
+              dalloc(&c->pos, c->np3) == cudaSuccess && dalloc(&c->mom, 3 * c->np3) == cudaSuccess &&
+              dalloc(&c->psi1, 3 * c->np3) == cudaSuccess && dalloc(&c->psi2, 3 * c->np3) == cudaSuccess &&
+              dalloc(&c->scratch, 9 * c->np3) == cudaSuccess && dalloc(&c->tw_m, (size_t)c->nm) == cudaSuccess &&
+              dalloc(&c->tw_p, (size_t)c->np) == cudaSuccess && dalloc(&c->sinc2_m, (size_t)c->nm) == cudaSuccess &&
+              dalloc(&c->amp_p, (size_t)3 * (c->np / 2) * (c->np / 2) + 1) == cudaSuccess &&
+              dalloc(&c->err, 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return COLAPM_E_NOMEM;
+    }
+    std::vector<float2> tm = twiddles(c->nm), tp = twiddles(c->np);
+    std::vector<float> s2(c->nm);
+    for (int i = 0; i < c->nm; ++i) {
+        const int s = i < c->nm / 2 ? i : i - c->nm;
+        const double x = M_PI * s / c->nm;
+        const double v = s == 0 ? 1.0 : std::sin(x) / x;
+        s2[i] = (float)(v * v);
+    }
+    // Gaussian-field amplitude N^3 sqrt(P(k) / L^3) per integer |n|^2 (FP64, then FP32).
+    const int h = c->np / 2, n2max = 3 * h * h;
+    std::vector<float> amp(n2max + 1);
+    LinearPk pk(p->cosmo.omega_m, p->cosmo.h, p->cosmo.n_s, p->cosmo.sigma8);
+    const double n3 = (double)c->np * c->np * c->np, l3 = p->box * p->box * p->box;
+    amp[0] = 0.0f;
+    for (int n2 = 1; n2 <= n2max; ++n2) amp[n2] = (float)(n3 * std::sqrt(pk(2.0 * M_PI * std::sqrt((double)n2) / p->box) / l3));
+    cudaError_t e = cudaMemcpyAsync(c->tw_m, tm.data(), tm.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->tw_p, tp.data(), tp.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->sinc2_m, s2.data(), s2.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->amp_p, amp.data(), amp.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, 4 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors die at return
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return COLAPM_E_CUDA;
+    }
+    *out = c;
+    return COLAPM_OK;
+}
+
+void colapm_destroy(colapm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+int colapm_make_ics(colapm_ctx* c) {
+    if (!c) return COLAPM_E_ARG;
+    Phase ph(c, COLAPM_PHASE_ICS);
+    const int np = c->np;
+    const size_t np3 = c->np3, hs = np3 / 2;   // complex elements per IC field
+    float2* dk = reinterpret_cast<float2*>(c->scratch);
+    float2* phi = reinterpret_cast<float2*>(c->scratch + np3);   // 6 fields
+    float2* p1 = reinterpret_cast<float2*>(c->psi1);
+    float2* p2 = reinterpret_cast<float2*>(c->psi2);
+    const float gnorm = (float)(1.0 / ((double)np * np * np));
+    CKL(launch_gaussian_field(np, c->prm.seed, c->amp_p, dk, c->stream));
+    ZOut o1{};
+    for (int j = 0; j < 3; ++j) o1.p[j] = p1 + j * hs;
+    for (int j = 0; j < 6; ++j) o1.p[3 + j] = phi + j * hs;
+    CKL(launch_fz(np, Z_LPT1, dk, o1, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream));
+    CKL(launch_fy(np, +1, p1, hs, 3, c->tw_p, c->stream));
+    CKL(launch_fy(np, +1, phi, hs, 6, c->tw_p, c->stream));
+    CKL(launch_fx_inv(np, p1, hs, 3, c->tw_p, c->stream));
+    CKL(launch_fx_inv(np, phi, hs, 6, c->tw_p, c->stream));
+    // 2LPT: S from the six phi_ij, then Psi2 = -i k S_k / k^2.
+    CKL(launch_lpt2_source(c->scratch + np3, np3, c->scratch, c->stream));
+    CKL(launch_fx_fwd_f32(np, c->scratch, phi, c->tw_p, c->stream));
+    CKL(launch_fy(np, -1, phi, 0, 1, c->tw_p, c->stream));
+    ZOut o2{};
+    for (int j = 0; j < 3; ++j) o2.p[j] = p2 + j * hs;
+    CKL(launch_fz(np, Z_LPT2, phi, o2, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream));
+    CKL(launch_fy(np, +1, p2, hs, 3, c->tw_p, c->stream));
+    CKL(launch_fx_inv(np, p2, hs, 3, c->tw_p, c->stream));
+    return place_particles(c, (float)c->nm / np);
+}
+
+int colapm_set_displacements(colapm_ctx* c, const float* psi1, const float* psi2) {
+    if (!c || !psi1 || !psi2) return COLAPM_E_ARG;
+    CK(cudaMemcpyAsync(c->psi1, psi1, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(c->psi2, psi2, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    int r = place_particles(c, (float)(c->nm / c->prm.box));
+    if (r) return r;
+    CK(cudaStreamSynchronize(c->stream));
+    return COLAPM_OK;
+}
+
+int colapm_step(colapm_ctx* c, int k) {
+    if (!c) return COLAPM_E_ARG;
+    if (!c->has_ics || c->finalized) return COLAPM_E_STATE;
+    const int left = c->prm.n_steps - c->step;
+    if (k < 0) k = left;
+    if (k > left) return COLAPM_E_STATE;
+    for (int s = 0; s < k; ++s) {
+        int r = compute_force(c);
+        if (r) return r;
+        Phase ph(c, COLAPM_PHASE_GATHER);
+        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, coef_for(c, c->step), 1,
+                                    c->stream));
+        ++c->step;
+    }
+    return COLAPM_OK;
+}
+
+int colapm_finalize(colapm_ctx* c) {
+    if (!c) return COLAPM_E_ARG;
+    if (!c->has_ics || c->finalized || c->step != c->prm.n_steps) return COLAPM_E_STATE;
+    int r = compute_force(c);
+    if (r) return r;
+    const int n = c->prm.n_steps;
+    const Growth& g = c->table.g[n];
+    StepCoef k{};
+    k.kick = (float)c->table.kick_final;
+    if (c->prm.cola) {
+        k.c1 = (float)g.d1;
+        k.c2 = (float)(g.d2 - g.d1 * g.d1);
+    }
+    {
+        Phase ph(c, COLAPM_PHASE_GATHER);
+        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, k, 0, c->stream));
+    }
+    if (c->prm.cola) CKL(launch_add_lpt_momentum(c->mom, c->psi1, c->psi2, c->np3, (float)g.p1, (float)g.p2, c->stream));
+    c->finalized = true;
+    return COLAPM_OK;
+}
+
+int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_out, double* p_out,
+                 long long* nmodes_out) {
+    if (!c || nbins < 1 || nbins > 4096 || !k_out || !p_out || !nmodes_out) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    const double box = c->prm.box, kf = 2.0 * M_PI / box;
+    if (kmin <= 0) kmin = kf;
+    if (kmax <= 0) kmax = M_PI * c->nm / box;
+    if (!(kmax > kmin)) return COLAPM_E_ARG;
+    const int h = c->nm / 2, n2max = 3 * h * h;
+    // Bin of every integer |n|^2, decided in FP64 with the same expressions as the definition:
+    // |k| = (2 pi / L) sqrt(n^2), edges e_b = kmin (kmax / kmin)^(b / nbins), e_b <= |k| < e_{b+1}.
+    std::vector<int> bin(n2max + 1, -1);
+    std::vector<double> kmag(n2max + 1);
+    std::vector<double> edges(nbins + 1);
+    for (int b = 0; b <= nbins; ++b) edges[b] = kmin * std::pow(kmax / kmin, (double)b / nbins);
+    for (int n2 = 0; n2 <= n2max; ++n2) {
+        const double km = kf * std::sqrt((double)n2);
+        kmag[n2] = km;
+        if (km < edges[0] || !(km < edges[nbins])) continue;
+        int lo = 0, hi = nbins;   // largest b with edges[b] <= km
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) / 2;
+            if (edges[mid] <= km) lo = mid; else hi = mid;
+        }
+        bin[n2] = lo;
+    }
+    if (n2max + 1 > c->pw_n2cap) {
+        if (c->pw_bin) cudaFree(c->pw_bin);
+        if (c->pw_kmag) cudaFree(c->pw_kmag);
+        c->pw_bin = nullptr;
+        c->pw_kmag = nullptr;
+        if (dalloc(&c->pw_bin, (size_t)n2max + 1) != cudaSuccess || dalloc(&c->pw_kmag, (size_t)n2max + 1) != cudaSuccess) {
+            c->pw_n2cap = 0;
+            return COLAPM_E_NOMEM;
+        }
+        c->pw_n2cap = n2max + 1;
+    }
+    if (nbins > c->pw_nbcap) {
+        if (c->pw_acc) cudaFree(c->pw_acc);
+        c->pw_acc = nullptr;
+        if (dalloc(&c->pw_acc, (size_t)3 * nbins) != cudaSuccess) {
+            c->pw_nbcap = 0;
+            return COLAPM_E_NOMEM;
+        }
+        c->pw_nbcap = nbins;
+    }
+    CK(cudaMemcpyAsync(c->pw_bin, bin.data(), bin.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->pw_kmag, kmag.data(), kmag.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->pw_acc, 0, (size_t)3 * nbins * sizeof(double), c->stream));
+    int r = deposit(c);
+    if (r) return r;
+    r = density_xy(c);
+    if (r) return r;
+    {
+        Phase ph(c, COLAPM_PHASE_POWER);
+        PowerArgs pw{};
+        pw.bin_of_n2 = c->pw_bin;
+        pw.kmag_of_n2 = c->pw_kmag;
+        pw.ksum = c->pw_acc;
+        pw.psum = c->pw_acc + nbins;
+        pw.cnt = reinterpret_cast<unsigned long long*>(c->pw_acc + 2 * nbins);
+        pw.nbins = nbins;
+        pw.n2max = n2max;
+        const double nm = c->nm;
+        pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
+        CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m, 0, 1.0f, &pw,
+                     c->stream));
+    }
+    std::vector<double> acc(3 * nbins);
+    CK(cudaMemcpyAsync(acc.data(), c->pw_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    r = pending_error(c);   // synchronises
+    if (r) return r;
+    std::vector<double> ko(nbins), po(nbins);
+    std::vector<long long> no(nbins);
+    for (int b = 0; b < nbins; ++b) {
+        unsigned long long cnt;
+        std::memcpy(&cnt, &acc[2 * nbins + b], sizeof(cnt));
+        no[b] = (long long)cnt;
+        ko[b] = cnt ? acc[b] / (double)cnt : NAN;
+        po[b] = cnt ? acc[nbins + b] / (double)cnt : NAN;
+    }
+    CK(cudaMemcpyAsync(k_out, ko.data(), nbins * sizeof(double), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(p_out, po.data(), nbins * sizeof(double), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(nmodes_out, no.data(), nbins * sizeof(long long), cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return COLAPM_OK;
+}
+
+int colapm_get_particles(colapm_ctx* c, float* pos, float* mom) {
+    if (!c) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    const float cell = (float)(c->prm.box / c->nm);
+    float* dp = pos && !is_device_ptr(pos) ? c->scratch : pos;
+    float* dm = mom && !is_device_ptr(mom) ? c->scratch + 3 * c->np3 : mom;
+    CKL(launch_export_particles(c->pos, c->mom, c->np3, c->nm, cell, dp, dm, c->stream));
+    if (pos && dp != pos) copy_out(c, pos, dp, 3 * c->np3 * sizeof(float));
+    if (mom && dm != mom) copy_out(c, mom, dm, 3 * c->np3 * sizeof(float));
+    return pending_error(c);
+}
+
+int colapm_get_state(colapm_ctx* c, int* cell, float* off, float* mom) {
+    if (!c) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    const size_t n = 3 * c->np3;
+    int* dc = cell && !is_device_ptr(cell) ? reinterpret_cast<int*>(c->scratch) : cell;
+    float* doff = off && !is_device_ptr(off) ? c->scratch + n : off;
+    float* dm = mom && !is_device_ptr(mom) ? c->scratch + 2 * n : mom;
+    CKL(launch_export_state(c->pos, c->mom, c->np3, c->nm, dc, doff, dm, c->stream));
+    if (cell && dc != cell) copy_out(c, cell, dc, n * sizeof(int));
+    if (off && doff != off) copy_out(c, off, doff, n * sizeof(float));
+    if (mom && dm != mom) copy_out(c, mom, dm, n * sizeof(float));
+    return pending_error(c);
+}
+
+int colapm_set_state(colapm_ctx* c, const int* cell, const float* off, const float* mom) {
+    if (!c || (!cell != !off) || (!cell && !mom)) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    const size_t n = 3 * c->np3;
+    const int* dc = cell;
+    const float* doff = off;
+    const float* dm = mom;
+    if (cell && !is_device_ptr(cell)) {
+        CK(cudaMemcpyAsync(c->scratch, cell, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        dc = reinterpret_cast<const int*>(c->scratch);
+    }
+    if (off && !is_device_ptr(off)) {
+        CK(cudaMemcpyAsync(c->scratch + n, off, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        doff = c->scratch + n;
+    }
+    if (mom && !is_device_ptr(mom)) {
+        CK(cudaMemcpyAsync(c->scratch + 2 * n, mom, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        dm = c->scratch + 2 * n;
+    }
+    CKL(launch_import_state(c->pos, c->mom, c->np3, c->nm, dc, doff, dm, c->err, c->stream));
+    return pending_error(c);
+}
+
+int colapm_get_density(colapm_ctx* c, long long* mesh) {
+    if (!c || !mesh) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    int r = deposit(c);
+    if (r) return r;
+    copy_out(c, mesh, c->rho, c->nm3 * sizeof(long long));
+    return pending_error(c);
+}
+
+int colapm_get_force(colapm_ctx* c, float* force) {
+    if (!c || !force) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    int r = compute_force(c);
+    if (r) return r;
+    copy_out(c, force, c->F, 3 * c->nm3 * sizeof(float));
+    return pending_error(c);
+}
+
+int colapm_get_lpt(colapm_ctx* c, float* psi1, float* psi2) {
+    if (!c) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    const float f = (float)(c->prm.box / c->nm);
+    const size_t n = 3 * c->np3;
+    if (psi1) {
+        CKL(launch_scale(c->scratch, c->psi1, n, f, c->stream));
+        copy_out(c, psi1, c->scratch, n * sizeof(float));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (psi2) {
+        CKL(launch_scale(c->scratch, c->psi2, n, f, c->stream));
+        copy_out(c, psi2, c->scratch, n * sizeof(float));
+    }
+    return pending_error(c);
+}
+
+int colapm_get_gaussian_field(colapm_ctx* c, float* dk) {
+    if (!c || !dk) return COLAPM_E_ARG;
+    CKL(launch_gaussian_field(c->np, c->prm.seed, c->amp_p, reinterpret_cast<float2*>(c->scratch), c->stream));
+    copy_out(c, dk, c->scratch, c->np3 * sizeof(float));
+    return pending_error(c);
+}
+
+int colapm_reseed(colapm_ctx* c, unsigned long long seed) {
+    if (!c) return COLAPM_E_ARG;
+    c->prm.seed = seed;
+    return COLAPM_OK;
+}
+
+long long colapm_kernel_launches(const colapm_ctx* c) { return c ? c->launches : COLAPM_E_ARG; }
+
+int colapm_sync(colapm_ctx* c) {
+    if (!c) return COLAPM_E_ARG;
+    return pending_error(c);
+}
+
+int colapm_steps_done(const colapm_ctx* c) { return c ? c->step : COLAPM_E_ARG; }
+
+static const unsigned long long kStateMagic = 0x434f4c41504d3031ull;   // "COLAPM01"
+
+int colapm_save_state(colapm_ctx* c, void* buf, size_t* n) {
+    if (!c || !n) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    const size_t hdr = 8 * sizeof(long long);
+    const size_t need = hdr + c->np3 * sizeof(float4) + 9 * c->np3 * sizeof(float);
+    if (!buf) {
+        *n = need;
+        return COLAPM_OK;
+    }
+    if (*n < need) return COLAPM_E_ARG;
+    long long h[8] = {(long long)kStateMagic, c->np, c->nm, c->step, c->finalized ? 1 : 0, c->prm.n_steps, 0, 0};
+    char* b = static_cast<char*>(buf);
+    std::memcpy(b, h, hdr);
+    size_t o = hdr;
+    CK(cudaMemcpyAsync(b + o, c->pos, c->np3 * sizeof(float4), cudaMemcpyDefault, c->stream));
+    o += c->np3 * sizeof(float4);
+    for (float* src : {c->mom, c->psi1, c->psi2}) {
+        CK(cudaMemcpyAsync(b + o, src, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->stream));
+        o += 3 * c->np3 * sizeof(float);
+    }
+    *n = need;
+    CK(cudaStreamSynchronize(c->stream));
+    return COLAPM_OK;
+}
+
+int colapm_load_state(colapm_ctx* c, const void* buf, size_t n) {
+    if (!c || !buf) return COLAPM_E_ARG;
+    const size_t hdr = 8 * sizeof(long long);
+    const size_t need = hdr + c->np3 * sizeof(float4) + 9 * c->np3 * sizeof(float);
+    if (n < need) return COLAPM_E_ARG;
+    long long h[8];
+    std::memcpy(h, buf, hdr);
+    if ((unsigned long long)h[0] != kStateMagic || h[1] != c->np || h[2] != c->nm || h[5] != c->prm.n_steps ||
+        h[3] < 0 || h[3] > c->prm.n_steps)
+        return COLAPM_E_ARG;
+    const char* b = static_cast<const char*>(buf);
+    size_t o = hdr;
+    CK(cudaMemcpyAsync(c->pos, b + o, c->np3 * sizeof(float4), cudaMemcpyDefault, c->stream));
+    o += c->np3 * sizeof(float4);
+    for (float* dst : {c->mom, c->psi1, c->psi2}) {
+        CK(cudaMemcpyAsync(dst, b + o, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->stream));
+        o += 3 * c->np3 * sizeof(float);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->step = (int)h[3];
+    c->finalized = h[4] != 0;
+    c->has_ics = true;
+    return COLAPM_OK;
+}
+
+int colapm_set_timing(colapm_ctx* c, int on) {
+    if (!c) return COLAPM_E_ARG;
+    c->timing = on != 0;
+    return COLAPM_OK;
+}
+
+int colapm_get_timing(colapm_ctx* c, double* ms, long long* launches) {
+    if (!c) return COLAPM_E_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < COLAPM_PHASE_COUNT; ++p) {
+        double sum = 0.0;
+        for (auto& pr : c->ev[p]) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) sum += t;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        if (ms) ms[p] = sum;
+        if (launches) launches[p] = (long long)c->ev[p].size();
+        c->ev[p].clear();
+    }
+    return COLAPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal declarations shared by the translation units of libcolapm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/colapm.h"
+
+namespace colapm {
+
+// Coefficients of one Kick-Drift step in mesh units (cells), converted from the FP64 table.
+struct StepCoef {
+    float kick;    // 1.5 Om times the kick integral (Quinn or modified, §2.3)
+    float c1;      // D1(a_i)            (COLA bracket; 0 for plain PM)
+    float c2;      // D2(a_i) - D1(a_i)^2 (COLA bracket; 0 for plain PM)
+    float drift;   // drift integral (§2.3)
+    float e1;      // D1(a_{i+1}) - D1(a_i) (COLA drift; 0 for plain PM)
+    float e2;      // D2(a_{i+1}) - D2(a_i)
+};
+
+// Output pointers of a z pass (up to 9 spectra: 3 x Psi1 and 6 x phi_ij of the ICs).
+struct ZOut {
+    float2* p[9];
+};
+
+enum ZMode {
+    Z_FORCE = 0,   // forward z, F_j = i k_j delta / (k^2 W^d) / N^3, inverse z, 3 outputs
+    Z_LPT1 = 1,    // (input already transformed) Psi1_j = i k_j d/k^2, phi_ab = k_a k_b d/k^2, 9 outputs
+    Z_LPT2 = 2,    // forward z, Psi2_j = -i k_j S/k^2, 3 outputs
+    Z_POWER = 3    // forward z, bin |delta|^2 / W^2
+};
+
+struct PowerArgs {
+    const int* bin_of_n2;       // bin index for integer |n|^2, -1 if outside
+    const double* kmag_of_n2;   // |k| for integer |n|^2
+    double* ksum;               // [nbins]
+    double* psum;               // [nbins]
+    unsigned long long* cnt;    // [nbins]
+    int nbins;
+    int n2max;
+    float pnorm;                // L^3 / N^6
+};
+
+// --- launchers (fft_kernels_*.cu) ----------------------------------------------------------
+// Forward x pass (r2c) of N^2 rows of N reals into N^2 rows of N/2 complex (Nyquist dropped).
+// in_i64: int64 fixed-point density converted to delta = rho * scale - 1 (flags err[0] bit 0
+// when a cell has its top bit set); in_f32: real field.
+cudaError_t launch_fx_fwd_i64(int n_mesh, const unsigned long long* in, float2* out, const float2* tw,
+                              float scale, int* err, cudaStream_t s);
+cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const float2* tw, cudaStream_t s);
+// Inverse x pass (c2r), in place, for `nfields` arrays spaced `field_stride` complex apart.
+cudaError_t launch_fx_inv(int n_mesh, float2* data, size_t field_stride, int nfields, const float2* tw,
+                          cudaStream_t s);
+// y pass in place (sign -1 forward, +1 inverse) on `nfields` arrays.
+cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
+                      cudaStream_t s);
+// z pass with the spectral multiply fused.
+cudaError_t launch_fz(int n_mesh, int mode, float2* in, ZOut out, const float2* tw, const float* sinc2,
+                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s);
+
+// --- launchers (pm_kernels.cu) --------------------------------------------------------------
+cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s);
+cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1, const float* psi2,
+                                     const float* force, size_t np3, int nm, StepCoef c, int drift,
+                                     cudaStream_t s);
+cudaError_t launch_init_particles(float4* pos, float* mom, float* psi1, float* psi2, int np, int nm,
+                                  float to_mesh, float d1, float d2, float p1, float p2, int cola,
+                                  cudaStream_t s);
+cudaError_t launch_add_lpt_momentum(float* mom, const float* psi1, const float* psi2, size_t np3, float p1,
+                                    float p2, cudaStream_t s);
+cudaError_t launch_export_particles(const float4* pos, const float* mom, size_t np3, int nm, float cell,
+                                    float* pos_xyz, float* mom_xyz, cudaStream_t s);
+cudaError_t launch_export_state(const float4* pos, const float* mom, size_t np3, int nm, int* cell_xyz,
+                                float* off_xyz, float* mom_xyz, cudaStream_t s);
+cudaError_t launch_import_state(float4* pos, float* mom, size_t np3, int nm, const int* cell_xyz,
+                                const float* off_xyz, const float* mom_xyz, int* err, cudaStream_t s);
+cudaError_t launch_scale(float* dst, const float* src, size_t n, float f, cudaStream_t s);
+
+// --- launchers (ics_kernels.cu) -----------------------------------------------------------
+cudaError_t launch_gaussian_field(int np, unsigned long long seed, const float* amp_of_n2, float2* dk,
+                                  cudaStream_t s);
+cudaError_t launch_lpt2_source(const float* phi, size_t np3, float* src, cudaStream_t s);
+
+}  // namespace colapm

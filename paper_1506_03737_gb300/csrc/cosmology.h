@@ -1,0 +1,36 @@
+// Host FP64 cosmology of the library (see cosmology.cpp).
+#pragma once
+
+#include <vector>
+
+namespace colapm {
+
+struct Growth {
+    double d1, d2, p1, p2;   // D1, D2 and P = a^3 E dD/da
+};
+
+Growth growth_at(double a, double om);
+
+struct StepTable {
+    std::vector<double> a;       // a_0 .. a_N
+    std::vector<Growth> g;       // growth at a_i
+    std::vector<double> kick;    // 1.5 Om x kick integral, step i
+    std::vector<double> drift;   // drift integral, step i
+    double kick_final = 0.0;     // closing half kick to a_N
+};
+
+// spacing: 0 linear in a, 1 logarithmic; stepping: 0 modified (nlpt), 1 Quinn.
+StepTable make_step_table(double om, double z_init, double z_final, int n_steps, int spacing, int stepping,
+                          double nlpt);
+
+class LinearPk {
+  public:
+    LinearPk(double om, double h, double ns, double sigma8);
+    double operator()(double k) const;   // (Mpc/h)^3 at z = 0, k in h/Mpc
+
+  private:
+    double shape(double k) const;
+    double om_, h_, ns_, amp_;
+};
+
+}  // namespace colapm

@@ -1,0 +1,284 @@
+// Particle kernels of the particle-mesh step (§2.3, §2.4 steps 1 and 4).
+//
+// Particle state (particle-id order): pos[p] = float4(offset_x, offset_y, offset_z, cell bits)
+// with the offsets in [0, 1) mesh cells and the linear cell index x + N (y + N z) stored in
+// the w word; mom, psi1, psi2 are component-major float arrays in mesh units (cells).
+//
+// Fixed-point CIC: f_q = rint(offset * 2^15) (round half to even); f_q = 2^15 moves the base
+// cell up by one with f_q = 0. Axis weights (2^15 - f_q, f_q); corner weight = their product
+// (scale 2^45), accumulated with 64-bit integer atomics, so the mesh is independent of the
+// order in which particles arrive. The gather uses the same weights divided by 2^45.
+#include "colapm_internal.h"
+
+namespace colapm {
+
+namespace {
+
+constexpr int QONE = 1 << 15;
+
+struct Cic {
+    int x0, y0, z0, x1, y1, z1;
+    int fx, fy, fz;
+};
+
+__device__ __forceinline__ Cic cic_setup(float4 P, int nm) {
+    const unsigned c = __float_as_uint(P.w);
+    const unsigned unm = (unsigned)nm;
+    int cx = (int)(c % unm), cy = (int)((c / unm) % unm), cz = (int)((c / (unm * unm)) % unm);
+    int fx = __float2int_rn(P.x * 32768.0f), fy = __float2int_rn(P.y * 32768.0f), fz = __float2int_rn(P.z * 32768.0f);
+    if (fx == QONE) { fx = 0; cx = cx + 1 == nm ? 0 : cx + 1; }
+    if (fy == QONE) { fy = 0; cy = cy + 1 == nm ? 0 : cy + 1; }
+    if (fz == QONE) { fz = 0; cz = cz + 1 == nm ? 0 : cz + 1; }
+    Cic r;
+    r.x0 = cx; r.y0 = cy; r.z0 = cz;
+    r.x1 = cx + 1 == nm ? 0 : cx + 1;
+    r.y1 = cy + 1 == nm ? 0 : cy + 1;
+    r.z1 = cz + 1 == nm ? 0 : cz + 1;
+    r.fx = fx; r.fy = fy; r.fz = fz;
+    return r;
+}
+
+__global__ void k_deposit(const float4* __restrict__ pos, size_t np3, int nm, unsigned long long* __restrict__ rho) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const Cic c = cic_setup(pos[p], nm);
+    const unsigned long long wx[2] = {(unsigned long long)(QONE - c.fx), (unsigned long long)c.fx};
+    const unsigned long long wy[2] = {(unsigned long long)(QONE - c.fy), (unsigned long long)c.fy};
+    const unsigned long long wz[2] = {(unsigned long long)(QONE - c.fz), (unsigned long long)c.fz};
+    const int xs[2] = {c.x0, c.x1}, ys[2] = {c.y0, c.y1}, zs[2] = {c.z0, c.z1};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const size_t row = ((size_t)zs[dz] * nm + ys[dy]) * nm;
+            const unsigned long long wyz = wy[dy] * wz[dz];
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const unsigned long long w = wx[dx] * wyz;
+                if (w) atomicAdd(rho + row + xs[dx], w);
+            }
+        }
+}
+
+__global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict__ mom, const float* __restrict__ psi1,
+                                    const float* __restrict__ psi2, const float* __restrict__ force, size_t np3, int nm,
+                                    StepCoef k, int drift) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    float4 P = pos[p];
+    const Cic c = cic_setup(P, nm);
+    const float s = 1.0f / 32768.0f;
+    const float wx[2] = {(QONE - c.fx) * s, c.fx * s};
+    const float wy[2] = {(QONE - c.fy) * s, c.fy * s};
+    const float wz[2] = {(QONE - c.fz) * s, c.fz * s};
+    const int xs[2] = {c.x0, c.x1}, ys[2] = {c.y0, c.y1}, zs[2] = {c.z0, c.z1};
+    const size_t m3 = (size_t)nm * nm * nm;
+    float f[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const size_t row = ((size_t)zs[dz] * nm + ys[dy]) * nm;
+            const float wyz = wy[dy] * wz[dz];
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const float w = wx[dx] * wyz;
+                const size_t i = row + xs[dx];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) f[j] = fmaf(w, __ldg(force + j * m3 + i), f[j]);
+            }
+        }
+    float d[3];
+    const float off[3] = {P.x, P.y, P.z};
+    int cell[3] = {(int)(__float_as_uint(P.w) % (unsigned)nm), (int)((__float_as_uint(P.w) / (unsigned)nm) % (unsigned)nm),
+                   (int)((__float_as_uint(P.w) / ((unsigned)nm * (unsigned)nm)) % (unsigned)nm)};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float s1 = psi1[j * np3 + p], s2 = psi2[j * np3 + p];
+        // kick (Eq. eq:vcola): p += K [F - D1 Psi1 - (D2 - D1^2) Psi2]
+        float v = mom[j * np3 + p];
+        v = fmaf(k.kick, f[j] - k.c1 * s1 - k.c2 * s2, v);
+        mom[j * np3 + p] = v;
+        // drift (Eq. eq:rcola): x += S p + dD1 Psi1 + dD2 Psi2
+        d[j] = drift ? fmaf(k.drift, v, fmaf(k.e1, s1, k.e2 * s2)) : 0.0f;
+    }
+    if (!drift) return;
+    float o[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float u = off[j] + d[j];
+        float fl = floorf(u);
+        float r = u - fl;
+        if (r >= 1.0f) { r = 0.0f; fl += 1.0f; }
+        int cc = (cell[j] + (int)fl) % nm;
+        if (cc < 0) cc += nm;
+        cell[j] = cc;
+        o[j] = r;
+    }
+    const unsigned lin = (unsigned)cell[0] + (unsigned)nm * ((unsigned)cell[1] + (unsigned)nm * (unsigned)cell[2]);
+    pos[p] = make_float4(o[0], o[1], o[2], __uint_as_float(lin));
+}
+
+// Particles on the Lagrangian lattice (offset by half a PM cell), displaced by D1 Psi1 + D2 Psi2.
+// psi1 / psi2 arrive in IC-grid cells and leave in PM-mesh cells (factor to_mesh = Nm / Np).
+__global__ void k_init_particles(float4* __restrict__ pos, float* __restrict__ mom, float* __restrict__ psi1,
+                                 float* __restrict__ psi2, int np, int nm, float to_mesh, float d1, float d2, float p1,
+                                 float p2, int cola) {
+    const size_t np3 = (size_t)np * np * np;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const int ratio = nm / np;
+    const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
+    int cell[3];
+    float o[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float s1 = psi1[j * np3 + p] * to_mesh, s2 = psi2[j * np3 + p] * to_mesh;
+        psi1[j * np3 + p] = s1;
+        psi2[j * np3 + p] = s2;
+        const float u = 0.5f + fmaf(d1, s1, d2 * s2);
+        float fl = floorf(u);
+        float r = u - fl;
+        if (r >= 1.0f) { r = 0.0f; fl += 1.0f; }
+        int cc = (site[j] * ratio + (int)fl) % nm;
+        if (cc < 0) cc += nm;
+        cell[j] = cc;
+        o[j] = r;
+        mom[j * np3 + p] = cola ? 0.0f : fmaf(p1, s1, p2 * s2);
+    }
+    const unsigned lin = (unsigned)cell[0] + (unsigned)nm * ((unsigned)cell[1] + (unsigned)nm * (unsigned)cell[2]);
+    pos[p] = make_float4(o[0], o[1], o[2], __uint_as_float(lin));
+}
+
+__global__ void k_add_lpt_momentum(float* __restrict__ mom, const float* __restrict__ psi1, const float* __restrict__ psi2,
+                                   size_t n3, float p1, float p2) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    mom[i] = fmaf(p1, psi1[i], fmaf(p2, psi2[i], mom[i]));
+}
+
+__global__ void k_export_particles(const float4* __restrict__ pos, const float* __restrict__ mom, size_t np3, int nm,
+                                   float cell, float* __restrict__ pos_xyz, float* __restrict__ mom_xyz) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    if (pos_xyz) {
+        const float4 P = pos[p];
+        const unsigned c = __float_as_uint(P.w), u = (unsigned)nm;
+        const unsigned cx = c % u, cy = (c / u) % u, cz = c / (u * u);
+        pos_xyz[3 * p + 0] = ((float)cx + P.x) * cell;
+        pos_xyz[3 * p + 1] = ((float)cy + P.y) * cell;
+        pos_xyz[3 * p + 2] = ((float)cz + P.z) * cell;
+    }
+    if (mom_xyz) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mom_xyz[3 * p + j] = mom[j * np3 + p] * cell;
+    }
+}
+
+__global__ void k_export_state(const float4* __restrict__ pos, const float* __restrict__ mom, size_t np3, int nm,
+                               int* __restrict__ cell_xyz, float* __restrict__ off_xyz, float* __restrict__ mom_xyz) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const float4 P = pos[p];
+    if (cell_xyz) {
+        const unsigned c = __float_as_uint(P.w), u = (unsigned)nm;
+        cell_xyz[3 * p + 0] = (int)(c % u);
+        cell_xyz[3 * p + 1] = (int)((c / u) % u);
+        cell_xyz[3 * p + 2] = (int)(c / (u * u));
+    }
+    if (off_xyz) {
+        off_xyz[3 * p + 0] = P.x;
+        off_xyz[3 * p + 1] = P.y;
+        off_xyz[3 * p + 2] = P.z;
+    }
+    if (mom_xyz) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mom_xyz[3 * p + j] = mom[j * np3 + p];
+    }
+}
+
+__global__ void k_import_state(float4* __restrict__ pos, float* __restrict__ mom, size_t np3, int nm,
+                               const int* __restrict__ cell_xyz, const float* __restrict__ off_xyz,
+                               const float* __restrict__ mom_xyz, int* err) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    if (cell_xyz && off_xyz) {
+        int c[3];
+        float o[3];
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            c[j] = cell_xyz[3 * p + j];
+            o[j] = off_xyz[3 * p + j];
+            bad |= !(c[j] >= 0 && c[j] < nm && o[j] >= 0.0f && o[j] < 1.0f);
+        }
+        if (bad) {
+            atomicOr(err, 2);
+            return;
+        }
+        const unsigned lin = (unsigned)c[0] + (unsigned)nm * ((unsigned)c[1] + (unsigned)nm * (unsigned)c[2]);
+        pos[p] = make_float4(o[0], o[1], o[2], __uint_as_float(lin));
+    }
+    if (mom_xyz) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) mom[j * np3 + p] = mom_xyz[3 * p + j];
+    }
+}
+
+__global__ void k_scale(float* __restrict__ dst, const float* __restrict__ src, size_t n, float f) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] * f;
+}
+
+inline unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s) {
+    k_deposit<<<blocks(np3, 256), 256, 0, s>>>(pos, np3, nm, rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1, const float* psi2, const float* force,
+                                     size_t np3, int nm, StepCoef c, int drift, cudaStream_t s) {
+    k_gather_kick_drift<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_particles(float4* pos, float* mom, float* psi1, float* psi2, int np, int nm, float to_mesh,
+                                  float d1, float d2, float p1, float p2, int cola, cudaStream_t s) {
+    const size_t np3 = (size_t)np * np * np;
+    k_init_particles<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, psi1, psi2, np, nm, to_mesh, d1, d2, p1, p2, cola);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_lpt_momentum(float* mom, const float* psi1, const float* psi2, size_t np3, float p1, float p2,
+                                    cudaStream_t s) {
+    k_add_lpt_momentum<<<blocks(3 * np3, 256), 256, 0, s>>>(mom, psi1, psi2, 3 * np3, p1, p2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_particles(const float4* pos, const float* mom, size_t np3, int nm, float cell,
+                                    float* pos_xyz, float* mom_xyz, cudaStream_t s) {
+    k_export_particles<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, np3, nm, cell, pos_xyz, mom_xyz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_state(const float4* pos, const float* mom, size_t np3, int nm, int* cell_xyz, float* off_xyz,
+                                float* mom_xyz, cudaStream_t s) {
+    k_export_state<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, np3, nm, cell_xyz, off_xyz, mom_xyz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_state(float4* pos, float* mom, size_t np3, int nm, const int* cell_xyz, const float* off_xyz,
+                                const float* mom_xyz, int* err, cudaStream_t s) {
+    k_import_state<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, np3, nm, cell_xyz, off_xyz, mom_xyz, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float* dst, const float* src, size_t n, float f, cudaStream_t s) {
+    k_scale<<<blocks(n, 256), 256, 0, s>>>(dst, src, n, f);
+    return cudaGetLastError();
+}
+
+}  // namespace colapm

@@ -1,0 +1,307 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: bit-exact for the int64 density mesh (integer work) and the mode counts; forces,
+positions and momenta within 1e-4 rms relative; P(k) within 1e-3 per bin for independent
+runs and 1e-4 on shared positions. Sizes span several FFT tiles with ragged tails and
+mixed radices (N_m = 96, 160, 192).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cola as ocola, cosmology as ocosmo, ics as oics, pm as opm, power as opower
+from paper_1506_03737_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_1506_03737_gb300 import colapm
+    return colapm
+
+
+class Sim:
+    def __init__(self, C, **kw):
+        self.C = C
+        self.p = C.default_params(**kw)
+        self.ctx = C.colapm_create(self.p)
+        self.np, self.nm, self.box = self.p.np, self.p.nm, self.p.box
+
+    def close(self):
+        self.C.colapm_destroy(self.ctx)
+
+    def state(self):
+        n = self.np ** 3
+        cell = np.empty((n, 3), np.int32)
+        off = np.empty((n, 3), np.float32)
+        mom = np.empty((n, 3), np.float32)
+        self.C.colapm_get_state(self.ctx, cell, off, mom)
+        return cell, off, mom
+
+    def lpt(self):
+        n = self.np ** 3
+        a, b = np.empty(3 * n, np.float32), np.empty(3 * n, np.float32)
+        self.C.colapm_get_lpt(self.ctx, a, b)
+        return a.reshape(3, self.np, self.np, self.np), b.reshape(3, self.np, self.np, self.np)
+
+    def density(self):
+        m = np.empty(self.nm ** 3, np.int64)
+        self.C.colapm_get_density(self.ctx, m)
+        return m.reshape(self.nm, self.nm, self.nm)
+
+    def force(self):
+        f = np.empty(3 * self.nm ** 3, np.float32)
+        self.C.colapm_get_force(self.ctx, f)
+        return f.reshape(3, self.nm, self.nm, self.nm)
+
+
+def mesh_coords(cell, off):
+    return cell.astype(np.float64) + off.astype(np.float64)
+
+
+def oracle_run(sim, **kw):
+    p = sim.p
+    r = ocola.Run(p.box, p.np, p.nm, p.cosmo.omega_m, p.z_init, p.z_final, p.n_steps,
+                  spacing="log" if p.spacing else "lin", stepping="quinn" if p.stepping else "modified",
+                  nlpt=p.nlpt, cola=bool(p.cola), deconv=p.deconv, **kw)
+    return r
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(np.mean((np.asarray(a, np.float64) - b) ** 2)) / np.sqrt(np.mean(np.asarray(b) ** 2)))
+
+
+# --- initial conditions ------------------------------------------------------------------
+
+@pytest.mark.parametrize("np_,seed", [(32, 1), (64, 9)])
+def test_gaussian_field_matches_oracle(C, np_, seed):
+    s = Sim(C, np=np_, nm=np_, box=256.0, seed=seed)
+    try:
+        dk = np.empty(np_ ** 3, np.float32)
+        C.colapm_get_gaussian_field(s.ctx, dk)
+        gpu = dk.view(np.complex64).reshape(np_, np_, np_ // 2).astype(np.complex128)
+        pk = ocosmo.linear_pk(0.3, 0.7, 0.96, 0.8)
+        ref = oics.gaussian_field(np_, 256.0, seed, pk)[:, :, : np_ // 2]
+        assert np.abs(gpu - ref).max() < 1e-5 * np.abs(ref).max()
+        assert np.array_equal(gpu == 0, ref == 0)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("np_,nm", [(32, 64), (64, 64)])
+def test_lpt_displacements_and_initial_positions(C, np_, nm):
+    s = Sim(C, np=np_, nm=nm, box=256.0, seed=4)
+    try:
+        C.colapm_make_ics(s.ctx)
+        g1, g2 = s.lpt()
+        pk = ocosmo.linear_pk(0.3, 0.7, 0.96, 0.8)
+        r = oracle_run(s)
+        dk = r.make_ics(4, pk)
+        psi1, psi2 = oics.lpt_displacements(dk, s.box)
+        assert rel_rms(g1, psi1) < 1e-5
+        assert rel_rms(g2, psi2) < 1e-4
+        cell, off, mom = s.state()
+        u = mesh_coords(cell, off)
+        ref_u = np.mod(r.x * nm / s.box, nm)
+        d = u - ref_u
+        d -= nm * np.rint(d / nm)
+        assert np.sqrt(np.mean(d ** 2)) < 1e-4 * np.sqrt(np.mean((r.displacement() * nm / s.box) ** 2))
+        assert not mom.any()                                   # COLA: residual momentum starts at 0
+    finally:
+        s.close()
+
+
+# --- deposit -------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("np_,nm,kind", [(32, 64, "random"), (32, 96, "random"), (64, 64, "clustered"),
+                                         (32, 160, "random")])
+def test_density_bit_exact(C, np_, nm, kind):
+    s = Sim(C, np=np_, nm=nm, box=200.0)
+    try:
+        C.colapm_make_ics(s.ctx)
+        gen = workloads.random_state if kind == "random" else workloads.clustered_state
+        cell, off, _ = gen(np_, nm, 11)
+        C.colapm_set_state(s.ctx, cell, off, None)
+        gpu = s.density()
+        ref = opm.cic_deposit(mesh_coords(cell, off), nm)
+        assert np.array_equal(gpu, ref)
+        assert gpu.sum() == np_ ** 3 << 45
+        assert np.array_equal(s.density(), gpu)                # deterministic across runs
+    finally:
+        s.close()
+
+
+# --- force ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("np_,nm,deconv", [(32, 64, 1), (32, 96, 1), (64, 128, 0), (32, 64, 2), (96, 192, 1)])
+def test_force_mesh_matches_oracle(C, np_, nm, deconv):
+    s = Sim(C, np=np_, nm=nm, box=300.0, deconv=deconv)
+    try:
+        C.colapm_make_ics(s.ctx)
+        cell, off, _ = workloads.clustered_state(np_, nm, 3)
+        C.colapm_set_state(s.ctx, cell, off, None)
+        gpu = s.force()
+        rho = opm.cic_deposit(mesh_coords(cell, off), nm)
+        ref = opm.force_mesh(opm.density_contrast(rho, np_, nm), s.box, deconv) * (nm / s.box)
+        for j in range(3):
+            assert rel_rms(gpu[j], ref[j]) < 1e-4, j
+    finally:
+        s.close()
+
+
+# --- one step from a shared state ----------------------------------------------------------
+
+@pytest.mark.parametrize("cola_on,stepping", [(1, 0), (0, 0), (1, 1)])
+def test_single_step_matches_oracle(C, cola_on, stepping):
+    np_, nm = 32, 64
+    s = Sim(C, np=np_, nm=nm, box=256.0, cola=cola_on, stepping=stepping, seed=5)
+    try:
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, 3)                       # evolve a little, then compare one step
+        cell, off, mom = s.state()
+        g1, g2 = s.lpt()
+        r = oracle_run(s)
+        r.set_displacements(g1.astype(np.float64), g2.astype(np.float64))
+        r.x = mesh_coords(cell, off) * s.box / nm
+        r.p = mom.astype(np.float64) * s.box / nm
+        r.step_index = 3
+        r.step()
+        C.colapm_step(s.ctx, 1)
+        cell2, off2, mom2 = s.state()
+        d = mesh_coords(cell2, off2) * s.box / nm - r.x
+        d -= s.box * np.rint(d / s.box)
+        move = mesh_coords(cell2, off2) - mesh_coords(cell, off)
+        move -= nm * np.rint(move / nm)
+        assert np.sqrt(np.mean(d ** 2)) < 1e-4 * np.sqrt(np.mean((move * s.box / nm) ** 2))
+        assert rel_rms(mom2 * s.box / nm, r.p) < 1e-4
+    finally:
+        s.close()
+
+
+# --- full runs ------------------------------------------------------------------------------
+
+def test_full_run_cola_32p_64m(C):
+    kw = workloads.run_params("cola_32p_64m_256mpc")
+    s = Sim(C, **kw)
+    try:
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, -1)
+        cell, off, mom = s.state()
+        r = oracle_run(s)
+        r.make_ics(kw["seed"], ocosmo.linear_pk(0.3, 0.7, 0.96, 0.8))
+        r.run()
+        d = mesh_coords(cell, off) * s.box / s.nm - r.x
+        d -= s.box * np.rint(d / s.box)
+        disp = np.sqrt(np.mean(r.displacement() ** 2))
+        assert np.sqrt(np.mean(d ** 2)) < 1e-4 * disp
+        k, pk, nmodes = C.colapm_power(s.ctx, 100)
+        kr, pr, nr = opower.power_from_positions(r.x, s.box, s.np, s.nm, 100)
+        assert np.array_equal(nmodes, nr)
+        ok = nr > 0
+        assert np.nanmax(np.abs(pk[ok] / pr[ok] - 1)) < 1e-3
+        assert np.nanmax(np.abs(k[ok] / kr[ok] - 1)) < 1e-12
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("nbins,kmin,kmax", [(100, 0.0, 0.0), (37, 0.05, 0.4), (12, 0.0, 2.0)])
+def test_power_on_shared_positions(C, nbins, kmin, kmax):
+    np_, nm = 32, 64
+    s = Sim(C, np=np_, nm=nm, box=256.0, seed=8)
+    try:
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, -1)
+        cell, off, _ = s.state()
+        k, pk, nmodes = C.colapm_power(s.ctx, nbins, kmin, kmax)
+        x = mesh_coords(cell, off) * s.box / nm
+        kr, pr, nr = opower.power_from_positions(x, s.box, np_, nm, nbins, kmin or None, kmax or None)
+        assert np.array_equal(nmodes, nr)
+        ok = nr > 0
+        assert np.max(np.abs(pk[ok] / pr[ok] - 1)) < 1e-4
+    finally:
+        s.close()
+
+
+def test_finalize_adds_lpt_momentum(C):
+    s = Sim(C, np=32, nm=64, box=256.0, n_steps=4, seed=6)
+    try:
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, -1)
+        cell, off, mom = s.state()
+        g1, g2 = s.lpt()
+        C.colapm_finalize(s.ctx)
+        pos, momf = np.empty((32 ** 3, 3), np.float32), np.empty((32 ** 3, 3), np.float32)
+        C.colapm_get_particles(s.ctx, pos, momf)
+        r = oracle_run(s)
+        r.set_displacements(g1.astype(np.float64), g2.astype(np.float64))
+        r.x = mesh_coords(cell, off) * s.box / s.nm
+        r.p = mom.astype(np.float64) * s.box / s.nm
+        r.step_index = 4
+        ref = r.finalize()
+        assert rel_rms(momf, ref) < 1e-4
+    finally:
+        s.close()
+
+
+# --- error paths and state I/O ----------------------------------------------------------------
+
+def test_error_codes(C):
+    with pytest.raises(C.ColapmError) as e:
+        C.colapm_create(C.default_params(np=33))
+    assert e.value.code == -1
+    with pytest.raises(C.ColapmError) as e:
+        C.colapm_create(C.default_params(np=64, nm=96))          # nm not a multiple of np
+    assert e.value.code == -1
+    s = Sim(C, np=16, nm=32)
+    try:
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_step(s.ctx, 1)                                # before ICs
+        assert e.value.code == -6
+        C.colapm_make_ics(s.ctx)
+        cell, off, _ = workloads.random_state(16, 32, 1)
+        off[10, 1] = 1.0                                          # out of range
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_set_state(s.ctx, cell, off, None)
+        assert e.value.code == -1
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_step(s.ctx, 11)
+        assert e.value.code == -6
+    finally:
+        s.close()
+
+
+def test_fixed_point_overflow_is_reported(C):
+    # 2^18 particles on one node put 2^63 into one cell: the top bit is set and the FFT pass flags it.
+    s = Sim(C, np=64, nm=64)
+    try:
+        C.colapm_make_ics(s.ctx)
+        n = 64 ** 3
+        C.colapm_set_state(s.ctx, np.zeros((n, 3), np.int32), np.zeros((n, 3), np.float32), None)
+        f = np.empty(3 * 64 ** 3, np.float32)
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_get_force(s.ctx, f)
+        assert e.value.code == -4
+    finally:
+        s.close()
+
+
+def test_checkpoint_resume_is_bit_exact(C):
+    kw = dict(np=32, nm=64, box=256.0, seed=12)
+    a, b = Sim(C, **kw), Sim(C, **kw)
+    try:
+        C.colapm_make_ics(a.ctx)
+        C.colapm_step(a.ctx, 4)
+        buf = C.colapm_save_state(a.ctx)
+        C.colapm_step(a.ctx, -1)
+        C.colapm_load_state(b.ctx, buf)
+        assert C.colapm_steps_done(b.ctx) == 4
+        C.colapm_step(b.ctx, -1)
+        assert np.array_equal(a.density(), b.density())
+        sa, sb = a.state(), b.state()
+        for x, y in zip(sa, sb):
+            assert np.array_equal(x, y)
+    finally:
+        a.close()
+        b.close()
