@@ -127,7 +127,7 @@ def test_density_bit_exact(C, np_, nm, kind):
         gpu = s.density()
         ref = opm.cic_deposit(mesh_coords(cell, off), nm)
         assert np.array_equal(gpu, ref)
-        assert gpu.sum() == np_ ** 3 << 45
+        assert int(gpu.astype(np.uint64).sum()) == np_ ** 3 << 45   # 2^63 for 64^3: sum unsigned
         assert np.array_equal(s.density(), gpu)                # deterministic across runs
     finally:
         s.close()
