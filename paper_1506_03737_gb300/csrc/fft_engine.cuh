@@ -141,9 +141,9 @@ struct Tile {
 };
 
 // One Stockham stage over a whole tile (all W lines), T threads.
-// tw: exp(-2 pi i t / TWN), t < TWN, with TWN a multiple of L (stride TWN / L).
+// tw: exp(-2 pi i t / TWN), t < TWN (shared or global memory), TWN a multiple of L.
 template <int L, int W, int T, bool LINE_MAJOR, int S, int NS, int R, int TWN>
-__device__ __forceinline__ void stockham_stage(float2* sm, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_stage(float2* sm, const float2* tw) {
     using TL = Tile<L, W, LINE_MAJOR>;
     constexpr int NB = (L / R) * W;             // butterflies in the tile
     constexpr int PER = (NB + T - 1) / T;       // butterflies per thread
@@ -160,7 +160,7 @@ __device__ __forceinline__ void stockham_stage(float2* sm, const float2* __restr
             for (int r = 0; r < R; ++r) {
                 float2 x = sm[TL::at(line, j + r * (L / R))];
                 if (NS > 1 && r > 0) {
-                    float2 w = __ldg(&tw[jm * r * (L / (NS * R)) * (TWN / L)]);   // < TWN
+                    float2 w = tw[jm * r * (L / (NS * R)) * (TWN / L)];   // index < TWN
                     x = cmul(x, S > 0 ? cconj(w) : w);
                 }
                 v[i][r] = x;
@@ -184,14 +184,14 @@ __device__ __forceinline__ void stockham_stage(float2* sm, const float2* __restr
 }
 
 template <int L, int W, int T, bool LINE_MAJOR, int S, int NS, int TWN, int R, int... Rest>
-__device__ __forceinline__ void stockham_run(float2* sm, const float2* __restrict__ tw, Radices<R, Rest...>) {
+__device__ __forceinline__ void stockham_run(float2* sm, const float2* tw, Radices<R, Rest...>) {
     stockham_stage<L, W, T, LINE_MAJOR, S, NS, R, TWN>(sm, tw);
     if constexpr (sizeof...(Rest) > 0) stockham_run<L, W, T, LINE_MAJOR, S, NS * R, TWN>(sm, tw, Radices<Rest...>{});
 }
 
 // Transform every line of the tile in place; the caller has synchronised after filling it.
 template <int L, int W, int T, bool LINE_MAJOR, int S, int TWN>
-__device__ __forceinline__ void tile_fft(float2* sm, const float2* __restrict__ tw) {
+__device__ __forceinline__ void tile_fft(float2* sm, const float2* tw) {
     stockham_run<L, W, T, LINE_MAJOR, S, 1, TWN>(sm, tw, typename Plan<L>::type{});
 }
 

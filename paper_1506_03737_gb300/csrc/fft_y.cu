@@ -3,21 +3,24 @@
 
 namespace colapm {
 
+template <int N, int S>
+static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
+    using C = YCfg<N>;
+    constexpr size_t smem = 2 * C::TILE_BYTES + C::TW_BYTES;
+    static int grid = 0;
+    if (!grid) {
+        cudaError_t e = set_smem(k_fy<N, S>, smem);
+        if (e != cudaSuccess) return e;
+        grid = persistent_grid(k_fy<N, S>, C::T, smem);
+    }
+    const int total = (N / 2 / kW) * N * nfields;
+    k_fy<N, S><<<grid < total ? grid : total, C::T, smem, s>>>(data, fstride, tw, nfields);
+    return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t fy_t(int sign, float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
-    using C = YCfg<N>;
-    dim3 grid(N / 2 / kW, N, (unsigned)nfields);
-    cudaError_t e;
-    if (sign < 0) {
-        static bool init = false;
-        if (!init) { e = set_smem(k_fy<N, -1>, C::SMEM); if (e != cudaSuccess) return e; init = true; }
-        k_fy<N, -1><<<grid, C::T, C::SMEM, s>>>(data, fstride, tw);
-    } else {
-        static bool init = false;
-        if (!init) { e = set_smem(k_fy<N, +1>, C::SMEM); if (e != cudaSuccess) return e; init = true; }
-        k_fy<N, +1><<<grid, C::T, C::SMEM, s>>>(data, fstride, tw);
-    }
-    return cudaGetLastError();
+    return sign < 0 ? fy_sign<N, -1>(data, fstride, nfields, tw, s) : fy_sign<N, +1>(data, fstride, nfields, tw, s);
 }
 
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
