@@ -182,6 +182,34 @@ int colapm_get_timing(colapm_ctx* ctx, double* ms, long long* launches);
 /* Number of CUDA kernels this context has launched so far (memsets and copies excluded). */
 long long colapm_kernel_launches(const colapm_ctx* ctx);
 
+/* Power spectrum of caller-owned particle positions without any allocation.
+ *
+ * The paper has no counterpart: this is a library convenience. It is for callers that cannot
+ * call cudaMalloc -- code that runs inside another framework's device-memory budget or custom
+ * allocator, or in a loop where cudaMalloc's implicit device synchronisation is not allowed --
+ * and so cannot create a context. It computes what colapm_power computes (same deposit,
+ * transform, binning and FP64 sums) for `n_particles` positions given as integer mesh cells
+ * (`cell`, xyz int32, each in [0, nm)) and offsets (`offset`, xyz float, each in [0, 1)), both
+ * DEVICE arrays owned by the caller; the mean density is n_particles / nm^3 per cell. Outputs
+ * (nbins each, host or device): mean |k|, mean P, mode count. kmin <= 0 selects 2 pi / box,
+ * kmax <= 0 selects pi nm / box.
+ *
+ * All working memory lives in one fixed device array inside the library, sized for
+ * nm <= COLAPM_NOALLOC_MAX_NM (one of 16, 32, 64, 96, 128) and nbins <= COLAPM_NOALLOC_MAX_BINS;
+ * larger sizes, host input arrays or positions out of range return COLAPM_E_ARG. Every GPU
+ * that loads the library holds that array (about 25 MB) until the process exits. The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). Every call
+ * shares the array and leaves the last call's contents in it; each call clears what must
+ * start at zero. Calls that overlap on the GPU (e.g. on two unordered streams) race on the
+ * array and must not be issued. The first call on a device looks up the array's device
+ * address for that device (once) and should come before any stream capture. Work runs on
+ * `stream` (a cudaStream_t, may be NULL); the call synchronises that stream before returning. */
+#define COLAPM_NOALLOC_MAX_NM 128
+#define COLAPM_NOALLOC_MAX_BINS 512
+int colapm_power_noalloc(const int* cell, const float* offset, long long n_particles, int nm, double box,
+                         int nbins, double kmin, double kmax, double* k_out, double* p_out,
+                         long long* nmodes_out, void* stream);
+
 /* Static message for an error code. */
 const char* colapm_strerror(int code);
 

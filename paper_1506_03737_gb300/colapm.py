@@ -63,6 +63,7 @@ def _load():
         "colapm_set_timing": (I, [P, I]),
         "colapm_get_timing": (I, [P, P, P]),
         "colapm_strerror": (ctypes.c_char_p, [I]),
+        "colapm_power_noalloc": (I, [P, P, ctypes.c_longlong, I, D, I, D, D, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +206,17 @@ def colapm_save_state(ctx):
 
 def colapm_load_state(ctx, buf):
     _check(LIB.colapm_load_state(ctx, _ptr(buf), buf.nbytes), "colapm_load_state")
+
+
+def colapm_power_noalloc(cell, offset, n_particles, nm, box, nbins, kmin=0.0, kmax=0.0, k_out=None, p_out=None,
+                         n_out=None, stream=0):
+    k_out = np.empty(nbins) if k_out is None else k_out
+    p_out = np.empty(nbins) if p_out is None else p_out
+    n_out = np.empty(nbins, dtype=np.int64) if n_out is None else n_out
+    _check(LIB.colapm_power_noalloc(_ptr(cell), _ptr(offset), n_particles, nm, box, nbins, kmin, kmax, _ptr(k_out),
+                                    _ptr(p_out), _ptr(n_out), ctypes.c_void_p(stream or None)),
+           "colapm_power_noalloc")
+    return k_out, p_out, n_out
 
 
 def colapm_set_timing(ctx, on=True):
