@@ -1,0 +1,515 @@
+// Two-stage register FFT for the large power-of-two mesh sizes (L = 256, 512, 1024).
+//
+// A line of length L = RA * RB (radices 16 or 32) is transformed in two Stockham stages. In
+// stage A (stride 1) task j < L/RA takes inputs j + r L/RA (r < RA) straight from global memory
+// (or from the caller), applies the RA-point DFT in registers and writes output r to position
+// j RA + r of a shared exchange buffer. In stage B (stride RA) task j < RA reads positions
+// j + r RA (r < RB), multiplies input r by w^(j r), w = exp(sign 2 pi i / L), applies the RB-point
+// DFT and holds output r = X[j + RA r] in registers, which the caller writes out. A line thus
+// crosses shared memory once (one 8-byte write and one read per element); the exchange buffer
+// pads every RA elements by one and every line to a pitch = 4 (mod 16) elements, so that the
+// two access patterns use the minimum number of bank wavefronts for both thread mappings used
+// (8 lines x 4 tasks per warp, or 32 tasks of one line per warp).
+//
+// Because the stage-B output of task j (X[j + RA r], r < RB) is exactly the stage-A input set
+// of task j of a transform with the radices swapped (RB, RA), an inverse transform can follow a
+// forward one on the same registers (the z pass chains forward, multiply, inverse).
+//
+// Twiddles w^(j r) come from two small shared tables, w^j (j < 32) and w^(8 m j) (m < 4, j < 32):
+// w^(j r) = w^(8 floor(r/8) j) * (w^j)^(r mod 8), at most 7 multiplications from a table value.
+#pragma once
+
+#include "fft_engine.cuh"
+
+namespace colapm {
+
+template <int L>
+struct F2;
+template <> struct F2<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct F2<512> { static constexpr int R1 = 16, R2 = 32; };
+template <> struct F2<1024> { static constexpr int R1 = 32, R2 = 32; };
+
+template <int L>
+struct F2Has { static constexpr bool value = L == 256 || L == 512 || L == 1024; };
+
+// Exchange buffer of 8 lines for a stage-A radix RA.
+template <int L, int RA>
+struct Xch {
+    static constexpr int PITCH = L + L / RA + 4;   // = 4 (mod 16) for the sizes above
+    static constexpr int SIZE = 8 * PITCH;         // float2 elements
+    __device__ __forceinline__ static int at(int c, int e) { return c * PITCH + e + e / RA; }
+};
+
+// Twiddle tables for length L: w1[j] = w^j, w8[m][j] = w^(8 m j), w = exp(-2 pi i / L).
+struct Tw2 {
+    float2 w1[32];
+    float2 w8[4][32];
+};
+template <int L, int TWN>
+__device__ __forceinline__ void load_tw2(Tw2* t, const float2* __restrict__ g, int T) {
+    for (int e = threadIdx.x; e < 32 * 5; e += T) {
+        const int m = e / 32, j = e % 32;
+        const int idx = m == 0 ? j : ((8 * (m - 1) * j) % L);
+        const float2 v = g[idx * (TWN / L)];
+        if (m == 0) t->w1[j] = v; else t->w8[m - 1][j] = v;
+    }
+}
+
+// Multiply v[r] by w^(S j r) for r < R (j < 32).
+template <int R, int S>
+__device__ __forceinline__ void twiddle2(float2* v, const Tw2* t, int j) {
+    float2 p[8];
+    float2 w1 = t->w1[j];
+    if (S > 0) w1 = cconj(w1);
+    p[0] = make_float2(1.0f, 0.0f);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) p[k] = cmul(p[k - 1], w1);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        float2 w = p[r & 7];
+        if (r >= 8) {
+            float2 b = t->w8[r >> 3][j];
+            if (S > 0) b = cconj(b);
+            w = (r & 7) ? cmul(b, w) : b;
+        }
+        v[r] = cmul(v[r], w);
+    }
+}
+
+}  // namespace colapm
+
+#include "colapm_internal.h"
+
+namespace colapm {
+
+template <int L>
+struct K2 {   // threads: the larger task count of the two stages (8 lines)
+    static constexpr int RA = F2<L>::R1, RB = F2<L>::R2;
+    static constexpr int TA = 8 * L / RA, TB = 8 * L / RB;
+    static constexpr int T = TA > TB ? TA : TB;
+};
+
+__device__ __forceinline__ int sbin(int i, int L) { return i < L / 2 ? i : i - L; }
+
+// Stage B of a line held in exchange buffer xb (stage-A radix RA), task j < RA of line c:
+// loads j + RA r, twiddles, RB-point DFT. Returns X[j + RA r] in v.
+template <int L, int RA, int RB, int S>
+__device__ __forceinline__ void stage_b(const float2* xb, const Tw2* tw, int c, int j, float2* v) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r) v[r] = xb[Xch<L, RA>::at(c, j + RA * r)];
+    twiddle2<RB, S>(v, tw, j);
+    dft<RB, S>(v);
+}
+
+// ---------------------------------------------------------------------------------------------
+// y pass (strided columns, stride n = L/2 complex), persistent over tiles of 8 columns.
+template <int L, int S>
+__global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, size_t fstride,
+                                                   const float2* __restrict__ tw, int nfields) {
+    using K = K2<L>;
+    constexpr int RA = K::RA, RB = K::RB, n = L / 2, NG = n / 8, TPF = NG * L;
+    extern __shared__ float4 smem4[];
+    float2* xb = reinterpret_cast<float2*>(smem4);
+    Tw2* tws = reinterpret_cast<Tw2*>(xb + Xch<L, RA>::SIZE);
+    load_tw2<L, L>(tws, tw, K::T);
+    __syncthreads();
+    const int total = TPF * nfields;
+    const int tid = threadIdx.x, c = tid & 7, j = tid >> 3;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int f = t / TPF, r0 = t % TPF;
+        float2* g = data + (size_t)f * fstride + (size_t)(r0 / NG) * L * n + (r0 % NG) * 8 + c;
+        if (tid < K::TA) {
+            float2 v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[r] = __ldcg(g + (size_t)(j + r * (L / RA)) * n);
+            dft<RA, S>(v);
+#pragma unroll
+            for (int r = 0; r < RA; ++r) xb[Xch<L, RA>::at(c, j * RA + r)] = v[r];
+        }
+        __syncthreads();
+        if (tid < K::TB) {
+            float2 v[RB];
+            stage_b<L, RA, RB, S>(xb, tws, c, j, v);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) g[(size_t)(j + RA * r) * n] = v[r];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// z pass with the spectral operator fused (see k_fz in fft_kernels.cuh for the algebra):
+// forward z (radices R1, R2) -> bases in registers -> inverse z (radices R2, R1) per base.
+template <int L, int MODE>
+struct Z2 {
+    static constexpr int R1 = F2<L>::R1, R2 = F2<L>::R2;
+    static constexpr int XS = Xch<L, R1>::SIZE > Xch<L, R2>::SIZE ? Xch<L, R1>::SIZE : Xch<L, R2>::SIZE;
+    static constexpr int NSAVE = MODE == Z_LPT1 ? 2 : (MODE == Z_POWER ? 0 : 1);   // saved bases B (, C)
+    static constexpr bool PREFETCH = MODE != Z_LPT1;                              // next tile via cp.async
+    static constexpr int PF = PREFETCH ? 8 * L : 0;                               // dense [z][8] buffer
+    static constexpr size_t SMEM = sizeof(float2) * ((size_t)XS * (1 + NSAVE) + PF) + sizeof(Tw2);
+};
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut out, const float2* __restrict__ tw,
+                                                   const float* __restrict__ sinc2, int deconv, float gnorm,
+                                                   PowerArgs pw) {
+    using Z = Z2<L, MODE>;
+    constexpr int R1 = Z::R1, R2 = Z::R2, n = L / 2, NG = n / 8, NTILE = NG * L;
+    constexpr int T = K2<L>::T;
+    extern __shared__ float4 smem4[];
+    float2* xb = reinterpret_cast<float2*>(smem4);
+    float2* save = xb + Z::XS;                                   // bases B (, C), layout Xch<L,R1>
+    float2* pf = xb + Z::XS * (1 + Z::NSAVE);                    // prefetched input tile [z][8]
+    Tw2* tws = reinterpret_cast<Tw2*>(pf + Z::PF);
+    double* ksum = reinterpret_cast<double*>(tws + 1);
+    double* psum = ksum + pw.nbins;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(psum + pw.nbins);
+    load_tw2<L, L>(tws, tw, T);
+    if constexpr (MODE == Z_POWER) {
+        for (int b = threadIdx.x; b < pw.nbins; b += T) {
+            ksum[b] = 0.0;
+            psum[b] = 0.0;
+            cnt[b] = 0ull;
+        }
+    }
+    __syncthreads();
+    const float kf = 6.283185307179586f / (float)L;
+    const size_t stride = (size_t)L * n;
+    const int tid = threadIdx.x, c = tid & 7, j = tid >> 3;
+    constexpr int TA = 8 * L / R1, TB = 8 * L / R2;   // forward stage-A / stage-B tasks
+    auto prefetch = [&](int tt) {   // 16-byte cp.async.cg of rows z = 0..L-1, 8 columns, into pf
+        const size_t b = (size_t)(tt / NG) * n + (tt % NG) * 8;
+        for (int e = tid; e < L * 4; e += T) {
+            const int z = e >> 2, q = e & 3;
+            cp_async16_cg(pf + z * 8 + 2 * q, in + b + (size_t)z * stride + 2 * q);
+        }
+        cp_async_commit();
+    };
+    if constexpr (Z::PREFETCH) {
+        if (blockIdx.x < NTILE) prefetch(blockIdx.x);
+    }
+
+    for (int t = blockIdx.x; t < NTILE; t += gridDim.x) {
+        const int ky = t / NG, kx0 = (t % NG) * 8;
+        const int ny = sbin(ky, L);
+        const bool nyq_y = (ky == L / 2);
+        const size_t base = (size_t)ky * n + kx0 + c;
+        const int nx = kx0 + c;
+        float2 v[R2];   // stage-B results: X[j + R1 r] (j < R1), or the LPT1 input spectrum
+        if constexpr (MODE == Z_LPT1) {
+            if (tid < TB) {
+#pragma unroll
+                for (int r = 0; r < R2; ++r) v[r] = __ldcg(in + base + (size_t)(j + R1 * r) * stride);
+            }
+        } else {
+            cp_async_wait<0>();
+            __syncthreads();
+            float2 a[R1];
+            if (tid < TA) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) a[r] = pf[(j + r * (L / R1)) * 8 + c];
+            }
+            __syncthreads();   // prefetch buffer consumed
+            if (t + (int)gridDim.x < NTILE) prefetch(t + gridDim.x);
+            if (tid < TA) {
+                dft<R1, -1>(a);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) xb[Xch<L, R1>::at(c, j * R1 + r)] = a[r];
+            }
+            __syncthreads();
+            if (tid < TB) stage_b<L, R1, R2, -1>(xb, tws, c, j, v);
+        }
+
+        if constexpr (MODE == Z_POWER) {
+            // Store the spectrum of the 8 columns in z order, then let each thread bin a run of
+            // consecutive z of one column, flushing when the bin changes.
+            if (tid < TB) {
+#pragma unroll
+                for (int r = 0; r < R2; ++r) xb[Xch<L, R1>::at(c, j + R1 * r)] = v[r];
+            }
+            __syncthreads();
+            constexpr int PER = L * 8 / T;
+            const int pc = tid % 8, z0 = (tid / 8) * PER, px = kx0 + pc;
+            if (!nyq_y) {
+                int rb = -1;
+                double rp = 0.0, rk = 0.0;   // FP64 sums of FP32 per-mode values
+                unsigned rc = 0;
+                const float mult = px == 0 ? 1.0f : 2.0f;   // conjugate twin with k_x -> -k_x
+#pragma unroll 8
+                for (int zz = 0; zz < PER; ++zz) {
+                    const int z = z0 + zz;
+                    if (z == L / 2) continue;
+                    const int nz = sbin(z, L);
+                    const int n2 = px * px + ny * ny + nz * nz;
+                    const int b = (n2 == 0 || n2 > pw.n2max) ? -1 : pw.bin_of_n2[n2];
+                    if (b < 0) continue;
+                    if (b != rb) {
+                        if (rb >= 0) {
+                            atomicAdd(&psum[rb], rp);
+                            atomicAdd(&ksum[rb], rk);
+                            atomicAdd(&cnt[rb], (unsigned long long)rc);
+                        }
+                        rb = b;
+                        rp = 0.0;
+                        rk = 0.0;
+                        rc = 0;
+                    }
+                    const float2 q = xb[Xch<L, R1>::at(pc, z)];
+                    const float w = sinc2[px] * sinc2[ky] * sinc2[z];
+                    rp += (double)(mult * (q.x * q.x + q.y * q.y) * pw.pnorm / (w * w));
+                    rk += (double)mult * pw.kmag_of_n2[n2];
+                    rc += px == 0 ? 1u : 2u;
+                }
+                if (rb >= 0) {
+                    atomicAdd(&psum[rb], rp);
+                    atomicAdd(&ksum[rb], rk);
+                    atomicAdd(&cnt[rb], (unsigned long long)rc);
+                }
+            }
+            __syncthreads();
+            continue;
+        } else {
+            // bases: A = g X, B = k_z A (, C = k_z^2 A); g = gnorm / (k^2 [W^d]), 0 on excluded modes
+            if (tid < TB) {
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    const int z = j + R1 * r;
+                    const int nz = sbin(z, L);
+                    float g = 0.0f;
+                    if (!nyq_y && z != L / 2 && (nx | ny | nz) != 0) {
+                        const float k2 = kf * kf * (float)(nx * nx + ny * ny + nz * nz);
+                        float w = 1.0f;
+                        if (MODE == Z_FORCE && deconv) {
+                            w = sinc2[nx] * sinc2[ky] * sinc2[z];
+                            if (deconv == 2) w *= w;
+                        }
+                        g = gnorm / (k2 * w);
+                    }
+                    v[r] = cscale(v[r], g);
+                    const float kz = kf * (float)nz;
+                    save[Xch<L, R1>::at(c, j + R1 * r)] = cscale(v[r], kz);
+                    if constexpr (Z::NSAVE == 2) save[Z::XS + Xch<L, R1>::at(c, j + R1 * r)] = cscale(v[r], kz * kz);
+                }
+            }
+            __syncthreads();   // forward exchange buffer free
+            const float kyv = kf * (float)ny;
+            const float kxv = kf * (float)nx;
+            constexpr float sg = MODE == Z_LPT2 ? -1.0f : 1.0f;
+            constexpr int NB = Z::NSAVE + 1;
+#pragma unroll 1
+            for (int bi = 0; bi < NB; ++bi) {
+                // inverse stage A (radix R2) on base bi held by task j < R1
+                if (tid < TB) {
+                    if (bi > 0) {
+#pragma unroll
+                        for (int r = 0; r < R2; ++r) v[r] = save[(bi - 1) * Z::XS + Xch<L, R1>::at(c, j + R1 * r)];
+                    }
+                    dft<R2, +1>(v);
+#pragma unroll
+                    for (int r = 0; r < R2; ++r) xb[Xch<L, R2>::at(c, j * R2 + r)] = v[r];
+                }
+                __syncthreads();
+                if (tid < TA) {   // inverse stage B (radix R1), task j < R2: outputs at j + R2 r
+                    float2 u[R1];
+                    stage_b<L, R2, R1, +1>(xb, tws, c, j, u);
+#pragma unroll
+                    for (int r = 0; r < R1; ++r) {
+                        const size_t o = base + (size_t)(j + R2 * r) * stride;
+                        const float2 a = u[r];
+                        const float2 ia = make_float2(-a.y, a.x);   // i * a
+                        if (bi == 0) {
+                            out.p[0][o] = cscale(ia, sg * kxv);
+                            out.p[1][o] = cscale(ia, sg * kyv);
+                            if constexpr (MODE == Z_LPT1) {
+                                out.p[3][o] = cscale(a, kxv * kxv);
+                                out.p[4][o] = cscale(a, kyv * kyv);
+                                out.p[6][o] = cscale(a, kxv * kyv);
+                            }
+                        } else if (bi == 1) {
+                            out.p[2][o] = cscale(ia, sg);
+                            if constexpr (MODE == Z_LPT1) {
+                                out.p[7][o] = cscale(a, kxv);
+                                out.p[8][o] = cscale(a, kyv);
+                            }
+                        } else {
+                            out.p[5][o] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if constexpr (MODE == Z_POWER) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < pw.nbins; b += T) {
+            if (cnt[b]) {
+                atomicAdd(&pw.psum[b], psum[b]);
+                atomicAdd(&pw.ksum[b], ksum[b]);
+                atomicAdd(&pw.cnt[b], cnt[b]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// x passes on rows of n complex (the N = 2n real rows), 8 rows per tile.
+template <int n>
+struct X2 {
+    static constexpr int RA = F2<n>::R1, RB = F2<n>::R2;
+    static constexpr int TA = 8 * n / RA, TB = 8 * n / RB, T = TA > TB ? TA : TB;
+    static constexpr size_t SMEM = sizeof(float2) * (size_t)Xch<n, RA>::SIZE + sizeof(Tw2);
+    // inverse: plus two dense [8][n] staging buffers for the cp.async prefetch of the rows
+    static constexpr size_t SMEM_INV = SMEM + 2 * sizeof(float2) * 8 * (size_t)n;
+};
+
+// forward r2c: in = int64 density pairs (I64, converted to rho * scale - 1) or float reals.
+template <int n, bool I64>
+__global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ in_, float2* __restrict__ out,
+                                                       const float2* __restrict__ tw, float scale, int* err,
+                                                       int nitems) {
+    using X = X2<n>;
+    constexpr int RA = X::RA, RB = X::RB, N = 2 * n;
+    extern __shared__ float4 smem4[];
+    float2* xb = reinterpret_cast<float2*>(smem4);
+    Tw2* tws = reinterpret_cast<Tw2*>(xb + Xch<n, RA>::SIZE);
+    load_tw2<n, N>(tws, tw, X::T);
+    __syncthreads();
+    const int tid = threadIdx.x;
+    bool over = false;
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        const size_t row0 = (size_t)t * 8;
+        if (tid < X::TA) {   // stage A: line c, task j (j fastest)
+            const int c = tid / (n / RA), j = tid % (n / RA);
+            float2 v[RA];
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                const size_t g = (row0 + c) * n + j + r * (n / RA);
+                if constexpr (I64) {
+                    const ulonglong2 q = __ldcs(reinterpret_cast<const ulonglong2*>(in_) + g);
+                    over |= ((q.x | q.y) >> 63) != 0;
+                    v[r] = make_float2(fmaf((float)(long long)q.x, scale, -1.0f), fmaf((float)(long long)q.y, scale, -1.0f));
+                } else {
+                    v[r] = __ldcg(reinterpret_cast<const float2*>(in_) + g);
+                }
+            }
+            dft<RA, -1>(v);
+#pragma unroll
+            for (int r = 0; r < RA; ++r) xb[Xch<n, RA>::at(c, j * RA + r)] = v[r];
+        }
+        __syncthreads();
+        if (tid < X::TB) {   // stage B in place: Z[j + RA r]
+            const int c = tid / RA, j = tid % RA;
+            float2 v[RB];
+            stage_b<n, RA, RB, -1>(xb, tws, c, j, v);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) xb[Xch<n, RA>::at(c, j + RA * r)] = v[r];
+        }
+        __syncthreads();
+        constexpr int H = n / 2 + 1;
+        for (int e = tid; e < 8 * H; e += X::T) {
+            const int c = e / H, k = e % H, k2 = (n - k) % n;
+            const float2 a = xb[Xch<n, RA>::at(c, k)], b = xb[Xch<n, RA>::at(c, k2)];
+            float2* o = out + (row0 + c) * n;
+            {   // X[k] from Z[k] = a, Z[n-k] = b; w^k = exp(-2 pi i k / N) = tw[k]
+                const float2 bc = cconj(b);
+                const float2 E = cscale(cadd(a, bc), 0.5f);
+                const float2 d = csub(a, bc);
+                o[k] = cadd(E, cmul(tw[k], make_float2(0.5f * d.y, -0.5f * d.x)));
+            }
+            if (k != 0 && k2 != k) {
+                const float2 ac = cconj(a);
+                const float2 E = cscale(cadd(b, ac), 0.5f);
+                const float2 d = csub(b, ac);
+                o[k2] = cadd(E, cmul(tw[k2], make_float2(0.5f * d.y, -0.5f * d.x)));
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (I64) {
+        if (over) atomicOr(err, 1);
+    }
+}
+
+// inverse c2r in place on `nfields` arrays; the next tile's rows are prefetched into a dense
+// [8][n] staging buffer with 16-byte cp.async while the current one is transformed.
+template <int n>
+__global__ void __launch_bounds__(X2<n>::T) k2_fx_inv(float2* __restrict__ data, size_t fstride,
+                                                       const float2* __restrict__ tw, int items_per_field,
+                                                       int nfields) {
+    using X = X2<n>;
+    constexpr int RA = X::RA, RB = X::RB, N = 2 * n, T = X::T;
+    extern __shared__ float4 smem4[];
+    float2* xb = reinterpret_cast<float2*>(smem4);
+    Tw2* tws = reinterpret_cast<Tw2*>(xb + Xch<n, RA>::SIZE);
+    float2* stg = reinterpret_cast<float2*>(tws + 1);   // 2 x [8][n]
+    load_tw2<n, N>(tws, tw, T);
+    const int tid = threadIdx.x;
+    const int nitems = items_per_field * nfields;
+    auto gptr = [&](int t) { return data + (size_t)(t / items_per_field) * fstride + (size_t)(t % items_per_field) * 8 * n; };
+    auto prefetch = [&](int t, int slot) {
+        const float2* g = gptr(t);
+        float2* d = stg + slot * 8 * n;
+        for (int e = tid; e < 8 * n / 2; e += T) cp_async16_cg(d + 2 * e, g + 2 * e);
+        cp_async_commit();
+    };
+    if (blockIdx.x < nitems) prefetch(blockIdx.x, 0);
+    int it = 0;
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++it) {
+        float2* d = gptr(t);
+        const float2* rows = stg + (it & 1) * 8 * n;
+        cp_async_wait<0>();
+        __syncthreads();
+        if (t + (int)gridDim.x < nitems) prefetch(t + gridDim.x, (it + 1) & 1);
+        constexpr int H = n / 2 + 1;
+        for (int e = tid; e < 8 * H; e += T) {   // Z'[k], Z'[n-k] from X[k], X[n-k] (X[n] = 0)
+            const int c = e / H, k = e % H;
+            const float2* row = rows + c * n;
+            const float2 xk = row[k];
+            if (k == 0) {
+                xb[Xch<n, RA>::at(c, 0)] = make_float2(xk.x - xk.y, xk.y + xk.x);   // X0 + i X0
+                continue;
+            }
+            const int k2 = n - k;
+            const float2 xk2 = row[k2];
+            {
+                const float2 xc = cconj(xk2);
+                const float2 E = cadd(xk, xc);
+                const float2 O = cmul(csub(xk, xc), cconj(tw[k]));
+                xb[Xch<n, RA>::at(c, k)] = make_float2(E.x - O.y, E.y + O.x);
+            }
+            if (k2 != k) {
+                const float2 xc = cconj(xk);
+                const float2 E = cadd(xk2, xc);
+                const float2 O = cmul(csub(xk2, xc), cconj(tw[k2]));
+                xb[Xch<n, RA>::at(c, k2)] = make_float2(E.x - O.y, E.y + O.x);
+            }
+        }
+        __syncthreads();
+        float2 v[RA];
+        const int ca = tid / (n / RA), ja = tid % (n / RA);
+        if (tid < X::TA) {
+#pragma unroll
+            for (int r = 0; r < RA; ++r) v[r] = xb[Xch<n, RA>::at(ca, ja + r * (n / RA))];
+            dft<RA, +1>(v);
+        }
+        __syncthreads();
+        if (tid < X::TA) {
+#pragma unroll
+            for (int r = 0; r < RA; ++r) xb[Xch<n, RA>::at(ca, ja * RA + r)] = v[r];
+        }
+        __syncthreads();
+        if (tid < X::TB) {
+            const int c = tid / RA, j = tid % RA;
+            float2 u[RB];
+            stage_b<n, RA, RB, +1>(xb, tws, c, j, u);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) d[(size_t)c * n + j + RA * r] = u[r];
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace colapm

@@ -1,24 +1,39 @@
 // Shared-memory Stockham FFT engine for the mesh transforms of the particle-mesh solver.
 //
-// The paper computes these transforms with FFTW-3 (§2.4 step 2, §4.3). Here each CTA
-// transforms a tile of lines held in shared memory: either W adjacent columns of a strided
-// axis ("column-major" tile, element (pos, col) at pos * (W + 1) + col, so that the W
-// contiguous complex values of one mesh row arrive in one coalesced load), or W whole
-// contiguous rows ("line-major" tile, element (line, pos) at line * LP + pos + pos / 16).
-// The paddings keep both the strided butterfly reads and the scattered Stockham writes of
-// 8-byte complex values within two shared-memory wavefronts per warp (column-major tiles
-// additionally need a first radix of at most 8).
+// The paper computes these transforms with FFTW-3 (§2.4 step 2, §4.3). Here each CTA transforms
+// a tile of 8 lines held in shared memory as L rows of 8 complex values (64 bytes per row): row
+// pos holds element pos of each of the 8 lines. A strided mesh axis maps 8 adjacent mesh columns
+// to one tile (each row is one coalesced 64-byte segment); a contiguous axis is transposed into
+// the same shape on load. Row r is stored at physical row r ^ (((r >> 2) ^ (r >> 3)) & 1): this
+// swaps the two rows of a 128-byte bank line when bits 2 and 3 of r differ, so that rows at
+// strides 1, 4 and 8 fall alternately into the two bank halves.
 //
+// Each thread works on two adjacent columns at once (one 16-byte shared access per element pair).
 // One stage of radix R at stride Ns (the product of the radices before it) takes, for every
-// butterfly j < L/R, the inputs j + r L/R, multiplies input r by w^((j mod Ns) r L/(Ns R))
-// with w = exp(sign 2 pi i / L), applies the R-point DFT in registers and writes output r
-// to (j / Ns) Ns R + (j mod Ns) + r Ns (Stockham autosort: natural order after the last
-// stage). Each stage reads all its inputs into registers, synchronises, then writes.
+// butterfly j < L/R, the inputs j + r L/R, multiplies input r by w^((j mod Ns) r L/(Ns R)) with
+// w = exp(sign 2 pi i / L), applies the R-point DFT in registers and writes output r to
+// (j / Ns) Ns R + (j mod Ns) + r Ns (Stockham autosort: natural order after the last stage).
+// With a first radix of 4 or 8 every stage's shared-memory accesses take the minimum number of
+// wavefronts. Each stage reads all of its inputs into registers, synchronises, then writes.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace colapm {
+
+__device__ __forceinline__ void cp_async8_ca(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -31,20 +46,19 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 template <int S>
 __device__ __forceinline__ float2 cmul_si(float2 a) { return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
 
+// cos and sin of 2 pi m / 32, m = 0..15 (mathematical constants rounded to float)
+#define COLAPM_C32(m) ((m) == 0 ? 1.0f : (m) == 1 ? 0.98078528040323044913f : (m) == 2 ? 0.92387953251128675613f : \
+    (m) == 3 ? 0.83146961230254523708f : (m) == 4 ? 0.70710678118654752440f : (m) == 5 ? 0.55557023301960222474f : \
+    (m) == 6 ? 0.38268343236508977173f : (m) == 7 ? 0.19509032201612826785f : (m) == 8 ? 0.0f : \
+    (m) == 9 ? -0.19509032201612826785f : (m) == 10 ? -0.38268343236508977173f : (m) == 11 ? -0.55557023301960222474f : \
+    (m) == 12 ? -0.70710678118654752440f : (m) == 13 ? -0.83146961230254523708f : (m) == 14 ? -0.92387953251128675613f : \
+    -0.98078528040323044913f)
+#define COLAPM_S32(m) ((m) == 0 ? 0.0f : COLAPM_C32(8 - (m) < 0 ? (m) - 8 : 8 - (m)))
+
 template <int R, int S>
-__device__ __forceinline__ float2 root(int k) {   // exp(S 2 pi i k / R), R in {2,4,8,16}, k < R/2
-    constexpr int step = 16 / R;
-    float c, s;
-    switch (k * step) {
-        case 0: c = 1.0f; s = 0.0f; break;
-        case 1: c = 0.92387953251128675613f; s = 0.38268343236508977173f; break;
-        case 2: c = 0.70710678118654752440f; s = 0.70710678118654752440f; break;
-        case 3: c = 0.38268343236508977173f; s = 0.92387953251128675613f; break;
-        case 4: c = 0.0f; s = 1.0f; break;
-        case 5: c = -0.38268343236508977173f; s = 0.92387953251128675613f; break;
-        case 6: c = -0.70710678118654752440f; s = 0.70710678118654752440f; break;
-        default: c = -0.92387953251128675613f; s = 0.38268343236508977173f; break;
-    }
+__device__ __forceinline__ float2 root(int k) {   // exp(S 2 pi i k / R), R in {2,4,8,16,32}, k < R/2 (unrolled)
+    const int m = k * (32 / R);
+    const float c = COLAPM_C32(m), s = COLAPM_S32(m);
     return make_float2(c, S > 0 ? s : -s);
 }
 
@@ -91,7 +105,7 @@ __device__ __forceinline__ void dft(float2* v) {
         v[2] = cadd(a2, ib2);
         v[3] = csub(a2, ib2);
     } else {
-        static_assert(R == 8 || R == 16, "unsupported radix");
+        static_assert(R == 8 || R == 16 || R == 32, "unsupported radix");
         float2 e[R / 2], o[R / 2];
 #pragma unroll
         for (int m = 0; m < R / 2; ++m) {
@@ -112,7 +126,7 @@ __device__ __forceinline__ void dft(float2* v) {
 template <int... Rs>
 struct Radices {};
 
-// Radix plan per transform length; column-major tiles need a first radix <= 8.
+// Radix plan per transform length (first radix 4 or 8).
 template <int L> struct Plan;
 template <> struct Plan<8> { using type = Radices<8>; };
 template <> struct Plan<16> { using type = Radices<4, 4>; };
@@ -121,51 +135,53 @@ template <> struct Plan<48> { using type = Radices<4, 4, 3>; };
 template <> struct Plan<64> { using type = Radices<8, 8>; };
 template <> struct Plan<80> { using type = Radices<4, 4, 5>; };
 template <> struct Plan<96> { using type = Radices<8, 4, 3>; };
-template <> struct Plan<128> { using type = Radices<8, 16>; };
+template <> struct Plan<128> { using type = Radices<8, 4, 4>; };
 template <> struct Plan<160> { using type = Radices<8, 4, 5>; };
 template <> struct Plan<192> { using type = Radices<8, 8, 3>; };
 template <> struct Plan<256> { using type = Radices<8, 8, 4>; };
 template <> struct Plan<320> { using type = Radices<8, 8, 5>; };
-template <> struct Plan<384> { using type = Radices<8, 16, 3>; };
+template <> struct Plan<384> { using type = Radices<8, 4, 4, 3>; };
 template <> struct Plan<512> { using type = Radices<8, 8, 8>; };
-template <> struct Plan<1024> { using type = Radices<8, 8, 16>; };
+template <> struct Plan<1024> { using type = Radices<8, 8, 4, 4>; };
 
-template <int L, int W, bool LINE_MAJOR>
-struct Tile {
-    static constexpr int LP = L + L / 16 + 1;                 // padded line (line-major)
-    static constexpr int PITCH = W + 1;                       // padded row (column-major)
-    static constexpr int SIZE = LINE_MAJOR ? W * LP : L * PITCH;
-    __device__ __forceinline__ static int at(int line, int pos) {
-        return LINE_MAJOR ? line * LP + pos + (pos >> 4) : pos * PITCH + line;
-    }
+// Tile of L rows x 8 complex columns.
+template <int L>
+struct CT {
+    static constexpr int SIZE = 8 * L;   // float2 elements
+    __device__ __forceinline__ static int prow(int r) { return r ^ (((r >> 2) ^ (r >> 3)) & 1); }
+    __device__ __forceinline__ static int a2(int r, int c) { return prow(r) * 8 + c; }   // float2 index
+    __device__ __forceinline__ static int a4(int r, int q) { return prow(r) * 4 + q; }   // float4 index
 };
 
-// One Stockham stage over a whole tile (all W lines), T threads.
+// One Stockham stage over the tile, T threads, each butterfly on a column pair.
 // tw: exp(-2 pi i t / TWN), t < TWN (shared or global memory), TWN a multiple of L.
-template <int L, int W, int T, bool LINE_MAJOR, int S, int NS, int R, int TWN>
+template <int L, int T, int S, int NS, int R, int TWN>
 __device__ __forceinline__ void stockham_stage(float2* sm, const float2* tw) {
-    using TL = Tile<L, W, LINE_MAJOR>;
-    constexpr int NB = (L / R) * W;             // butterflies in the tile
-    constexpr int PER = (NB + T - 1) / T;       // butterflies per thread
-    float2 v[PER][R];
+    constexpr int NB = (L / R) * 4;
+    constexpr int PER = (NB + T - 1) / T;
+    float4* s4 = reinterpret_cast<float4*>(sm);
+    float2 va[PER][R], vb[PER][R];
     const int tid = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int b = tid + i * T;
         if (NB % T == 0 || b < NB) {
-            const int line = LINE_MAJOR ? b / (L / R) : b % W;
-            const int j = LINE_MAJOR ? b % (L / R) : b / W;
-            const int jm = j % NS;
+            const int q = b & 3, j = b >> 2, jm = j % NS;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float2 x = sm[TL::at(line, j + r * (L / R))];
+                const float4 x = s4[CT<L>::a4(j + r * (L / R), q)];
+                float2 a = make_float2(x.x, x.y), c = make_float2(x.z, x.w);
                 if (NS > 1 && r > 0) {
                     float2 w = tw[jm * r * (L / (NS * R)) * (TWN / L)];   // index < TWN
-                    x = cmul(x, S > 0 ? cconj(w) : w);
+                    if (S > 0) w = cconj(w);
+                    a = cmul(a, w);
+                    c = cmul(c, w);
                 }
-                v[i][r] = x;
+                va[i][r] = a;
+                vb[i][r] = c;
             }
-            dft<R, S>(v[i]);
+            dft<R, S>(va[i]);
+            dft<R, S>(vb[i]);
         }
     }
     __syncthreads();
@@ -173,26 +189,26 @@ __device__ __forceinline__ void stockham_stage(float2* sm, const float2* tw) {
     for (int i = 0; i < PER; ++i) {
         const int b = tid + i * T;
         if (NB % T == 0 || b < NB) {
-            const int line = LINE_MAJOR ? b / (L / R) : b % W;
-            const int j = LINE_MAJOR ? b % (L / R) : b / W;
+            const int q = b & 3, j = b >> 2;
             const int d = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[TL::at(line, d + r * NS)] = v[i][r];
+            for (int r = 0; r < R; ++r)
+                s4[CT<L>::a4(d + r * NS, q)] = make_float4(va[i][r].x, va[i][r].y, vb[i][r].x, vb[i][r].y);
         }
     }
     __syncthreads();
 }
 
-template <int L, int W, int T, bool LINE_MAJOR, int S, int NS, int TWN, int R, int... Rest>
+template <int L, int T, int S, int NS, int TWN, int R, int... Rest>
 __device__ __forceinline__ void stockham_run(float2* sm, const float2* tw, Radices<R, Rest...>) {
-    stockham_stage<L, W, T, LINE_MAJOR, S, NS, R, TWN>(sm, tw);
-    if constexpr (sizeof...(Rest) > 0) stockham_run<L, W, T, LINE_MAJOR, S, NS * R, TWN>(sm, tw, Radices<Rest...>{});
+    stockham_stage<L, T, S, NS, R, TWN>(sm, tw);
+    if constexpr (sizeof...(Rest) > 0) stockham_run<L, T, S, NS * R, TWN>(sm, tw, Radices<Rest...>{});
 }
 
-// Transform every line of the tile in place; the caller has synchronised after filling it.
-template <int L, int W, int T, bool LINE_MAJOR, int S, int TWN>
+// Transform the 8 lines of the tile in place; the caller has synchronised after filling it.
+template <int L, int T, int S, int TWN>
 __device__ __forceinline__ void tile_fft(float2* sm, const float2* tw) {
-    stockham_run<L, W, T, LINE_MAJOR, S, 1, TWN>(sm, tw, typename Plan<L>::type{});
+    stockham_run<L, T, S, 1, TWN>(sm, tw, typename Plan<L>::type{});
 }
 
 }  // namespace colapm

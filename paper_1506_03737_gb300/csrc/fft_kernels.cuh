@@ -14,9 +14,11 @@
 // unnormalised inverse. The 1/N^3 of the inverse transform is folded into the z-pass
 // multiplier.
 //
-// Strided passes (y, z) run persistent CTAs over column tiles (kW adjacent columns, all L
-// positions) with the next tile prefetched by cp.async into a second shared buffer while the
-// current one is transformed.
+// Every pass is a persistent kernel over tiles of 8 lines (8 mesh rows for x, 8 adjacent
+// columns for y and z) that prefetches the next tile with cp.async into a second shared buffer
+// while the current one is transformed. Column tiles are copied with 16-byte cp.async.cg
+// (L2 only), row tiles with 8-byte cp.async.ca, the int64 density through a 16-byte staging
+// tile.
 #pragma once
 
 #include "colapm_internal.h"
@@ -24,208 +26,287 @@
 
 namespace colapm {
 
-constexpr int kW = 8;   // columns per strided tile (8 complex = 64 contiguous bytes per row)
-
-__host__ __device__ constexpr int pow2_floor(int v) {
-    int p = 1;
-    while (p * 2 <= v) p *= 2;
-    return p;
-}
-
-template <int n>
-struct XCfg {   // x pass: WX whole rows of n complex per CTA
-    static constexpr int N = 2 * n;
-    static constexpr int WA = pow2_floor(4096 / n);
-    static constexpr int WX = WA < 4 * n * n ? WA : 4 * n * n;
-    static constexpr int T = 256;
-    using TL = Tile<n, WX, true>;
-};
-
 template <int L>
-struct YCfg {   // strided passes: kW columns of length L per tile
-    static constexpr int T0 = L * kW / 16;
+struct TCfg {   // threads for a tile of L rows (each butterfly covers a column pair)
+    static constexpr int T0 = L / 2;
     static constexpr int T = T0 < 64 ? 64 : (T0 > 512 ? 512 : T0);
-    using TL = Tile<L, kW, false>;
-    static constexpr size_t TILE_BYTES = sizeof(float2) * TL::SIZE;
-    static constexpr size_t TW_BYTES = sizeof(float2) * L;
+    static constexpr size_t TILE = sizeof(float2) * 8 * L;
 };
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+// ---- tile I/O --------------------------------------------------------------------------------
+// Column tile: row r <- g[r * stride + 0..7] (complex).
+template <int L, int T>
+__device__ __forceinline__ void ld_cols(float2* sm, const float2* g, size_t stride) {
+    float4* s4 = reinterpret_cast<float4*>(sm);
+    for (int e = threadIdx.x; e < L * 4; e += T) {
+        const int r = e >> 2, q = e & 3;
+        cp_async16_cg(s4 + CT<L>::a4(r, q), g + (size_t)r * stride + 2 * q);
+    }
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+// out[r * stride + c] = f(c) * tile[r][c] (IMAG: times i).
+template <int L, int T, bool IMAG, typename F>
+__device__ __forceinline__ void st_cols_scaled(const float2* sm, float2* g, size_t stride, F f) {
+    const float4* s4 = reinterpret_cast<const float4*>(sm);
+    for (int e = threadIdx.x; e < L * 4; e += T) {
+        const int r = e >> 2, q = e & 3;
+        const float4 v = s4[CT<L>::a4(r, q)];
+        const float sa = f(2 * q), sb = f(2 * q + 1);
+        float4 o;
+        if constexpr (IMAG)
+            o = make_float4(-sa * v.y, sa * v.x, -sb * v.w, sb * v.z);
+        else
+            o = make_float4(sa * v.x, sa * v.y, sb * v.z, sb * v.w);
+        *reinterpret_cast<float4*>(g + (size_t)r * stride + 2 * q) = o;
+    }
+}
+template <int L, int T>
+__device__ __forceinline__ void st_cols(const float2* sm, float2* g, size_t stride) {
+    const float4* s4 = reinterpret_cast<const float4*>(sm);
+    for (int e = threadIdx.x; e < L * 4; e += T) {
+        const int r = e >> 2, q = e & 3;
+        *reinterpret_cast<float4*>(g + (size_t)r * stride + 2 * q) = s4[CT<L>::a4(r, q)];
+    }
+}
+// Row staging: 8 lines of n contiguous complex, copied with coalesced 16-byte cp.async into a
+// row-major buffer with a pitch of n + 4 elements (8-byte elements; a warp touching 8 lines x 4
+// positions then spreads over all banks), and transposed through shared memory into the column
+// tile. ESZ is the element size in bytes (8 for complex float, 16 for an int64 pair).
+template <int n, int ESZ>
+struct RowStage {
+    static constexpr int PITCH = n + (ESZ == 8 ? 4 : 2);     // elements per staged line
+    static constexpr size_t BYTES = (size_t)8 * PITCH * ESZ;
+};
+template <int n, int T, int ESZ>
+__device__ __forceinline__ void ld_rows_stage(unsigned char* stg, const unsigned char* g) {
+    constexpr int CH = n * ESZ / 16;   // 16-byte chunks per line
+    for (int e = threadIdx.x; e < 8 * CH; e += T) {
+        const int c = e / CH, k = e % CH;
+        cp_async16_cg(stg + ((size_t)c * RowStage<n, ESZ>::PITCH * ESZ + (size_t)k * 16), g + ((size_t)c * n * ESZ + (size_t)k * 16));
+    }
+}
+// staged complex rows -> column tile
+template <int n, int T>
+__device__ __forceinline__ void stage_to_tile(float2* tile, const float2* stg) {
+    for (int e = threadIdx.x; e < n * 8; e += T) {
+        const int c = e & 7, p = e >> 3;
+        tile[CT<n>::a2(p, c)] = stg[c * RowStage<n, 8>::PITCH + p];
+    }
+}
+// column tile -> staged rows -> coalesced 16-byte stores of 8 lines of n complex at g
+template <int n, int T>
+__device__ __forceinline__ void tile_to_rows(const float2* tile, float2* stg, float2* g) {
+    for (int e = threadIdx.x; e < n * 8; e += T) {
+        const int c = e & 7, p = e >> 3;
+        stg[c * RowStage<n, 8>::PITCH + p] = tile[CT<n>::a2(p, c)];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 8 * (n / 2); e += T) {
+        const int c = e / (n / 2), k = e % (n / 2);
+        *reinterpret_cast<float4*>(g + (size_t)c * n + 2 * k) =
+            *reinterpret_cast<const float4*>(stg + c * RowStage<n, 8>::PITCH + 2 * k);
+    }
 }
 
-// ---------------------------------------------------------------------------------------
-// x pass, forward (r2c). in: int64 density (I64) or float reals; out: n complex per row.
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Persistent grid: resident CTAs per SM x SMs.
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    if (per < 1) per = 1;
+    return per * sms;
+}
+
+// ---------------------------------------------------------------------------------------------
+// x passes: threads per CTA (the stages use n/2 of them; the copies and transposes all).
+template <int n>
+struct XT {
+    static constexpr int T = n < 64 ? 64 : (n > 512 ? 512 : n);
+};
+
+// x pass, forward (r2c), persistent over groups of 8 rows. in: int64 density (I64) converted
+// to delta = rho * scale - 1 (err bit 0 when a cell has its top bit set), or float reals.
 template <int n, bool I64>
-__global__ void __launch_bounds__(256) k_fx_fwd(const void* __restrict__ in_, float2* __restrict__ out,
-                                                const float2* __restrict__ tw, float scale, int* err) {
-    using C = XCfg<n>;
-    using TL = typename C::TL;
-    __shared__ float2 sm[TL::SIZE];
-    __shared__ float2 stw[C::N];
-    for (int e = threadIdx.x; e < C::N; e += C::T) stw[e] = tw[e];
-    const size_t row0 = (size_t)blockIdx.x * C::WX;
+struct FxFwd {
+    static constexpr int N = 2 * n, T = XT<n>::T;
+    using In = RowStage<n, I64 ? 16 : 8>;
+    using Out = RowStage<n, 8>;
+    static constexpr size_t SMEM = 2 * In::BYTES + TCfg<n>::TILE + sizeof(float2) * N;
+};
+
+template <int n, bool I64>
+__global__ void __launch_bounds__(XT<n>::T) k_fx_fwd(const void* __restrict__ in_, float2* __restrict__ out,
+                                                      const float2* __restrict__ tw, float scale, int* err,
+                                                      int nitems) {
+    using C = FxFwd<n, I64>;
+    constexpr int T = C::T, N = C::N, ESZ = I64 ? 16 : 8;
+    extern __shared__ float4 smem4[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(smem4);
+    float2* tile = reinterpret_cast<float2*>(base + 2 * C::In::BYTES);
+    float2* stw = tile + 8 * n;
+    for (int e = threadIdx.x; e < N; e += T) stw[e] = tw[e];
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(in_);
+    int t = blockIdx.x;
+    if (t < nitems) ld_rows_stage<n, T, ESZ>(base, src + (size_t)t * 8 * n * ESZ);
+    cp_async_commit();
     bool over = false;
-    for (int e = threadIdx.x; e < C::WX * n; e += C::T) {
-        const int line = e / n, m = e % n;
-        const size_t g = (row0 + line) * n + m;
-        float2 z;
+    for (int it = 0; t < nitems; t += gridDim.x, ++it) {
+        unsigned char* stg = base + (it & 1) * C::In::BYTES;
+        const int tn = t + gridDim.x;
+        if (tn < nitems) ld_rows_stage<n, T, ESZ>(base + ((it + 1) & 1) * C::In::BYTES, src + (size_t)tn * 8 * n * ESZ);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
         if constexpr (I64) {
-            const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(in_) + g);
-            over |= ((v.x | v.y) >> 63) != 0;
-            z.x = fmaf((float)(long long)v.x, scale, -1.0f);
-            z.y = fmaf((float)(long long)v.y, scale, -1.0f);
+            const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(stg);
+            for (int e = threadIdx.x; e < n * 8; e += T) {
+                const int c = e & 7, p = e >> 3;
+                const ulonglong2 v = s2[c * C::In::PITCH + p];
+                over |= ((v.x | v.y) >> 63) != 0;
+                tile[CT<n>::a2(p, c)] =
+                    make_float2(fmaf((float)(long long)v.x, scale, -1.0f), fmaf((float)(long long)v.y, scale, -1.0f));
+            }
         } else {
-            z = reinterpret_cast<const float2*>(in_)[g];
+            stage_to_tile<n, T>(tile, reinterpret_cast<const float2*>(stg));
         }
-        sm[TL::at(line, m)] = z;
+        __syncthreads();
+        tile_fft<n, T, -1, N>(tile, stw);
+        constexpr int H = n / 2 + 1;
+        for (int e = threadIdx.x; e < 8 * H; e += T) {
+            const int c = e & 7, k = e >> 3;
+            const int k2 = (n - k) % n;
+            const float2 a = tile[CT<n>::a2(k, c)], b = tile[CT<n>::a2(k2, c)];
+            {   // X[k] from Z[k] = a, Z[n-k] = b
+                const float2 bc = cconj(b);
+                const float2 E = cscale(cadd(a, bc), 0.5f);
+                const float2 d = csub(a, bc);
+                tile[CT<n>::a2(k, c)] = cadd(E, cmul(stw[k], make_float2(0.5f * d.y, -0.5f * d.x)));
+            }
+            if (k != 0 && k2 != k) {   // X[n-k] from Z[n-k] = b, Z[k] = a
+                const float2 ac = cconj(a);
+                const float2 E = cscale(cadd(b, ac), 0.5f);
+                const float2 d = csub(b, ac);
+                tile[CT<n>::a2(k2, c)] = cadd(E, cmul(stw[k2], make_float2(0.5f * d.y, -0.5f * d.x)));
+            }
+        }
+        __syncthreads();
+        tile_to_rows<n, T>(tile, reinterpret_cast<float2*>(stg), out + (size_t)t * 8 * n);
+        __syncthreads();
     }
+    cp_async_wait<0>();
     if constexpr (I64) {
         if (over) atomicOr(err, 1);
     }
-    __syncthreads();
-    tile_fft<n, C::WX, C::T, true, -1, C::N>(sm, stw);
-    constexpr int H = n / 2 + 1;
-    for (int e = threadIdx.x; e < C::WX * H; e += C::T) {
-        const int line = e / H, k = e % H;
-        const int k2 = (n - k) % n;
-        const float2 a = sm[TL::at(line, k)], b = sm[TL::at(line, k2)];
-        float2* o = out + (row0 + line) * n;
-        {   // X[k] from Z[k] = a, Z[n-k] = b
-            const float2 bc = cconj(b);
-            const float2 E = cscale(cadd(a, bc), 0.5f);
-            const float2 d = csub(a, bc);
-            const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);
-            o[k] = cadd(E, cmul(stw[k], O));
-        }
-        if (k != 0 && k2 != k) {   // X[n-k] from Z[n-k] = b, Z[k] = a
-            const float2 ac = cconj(a);
-            const float2 E = cscale(cadd(b, ac), 0.5f);
-            const float2 d = csub(b, ac);
-            const float2 O = make_float2(0.5f * d.y, -0.5f * d.x);
-            o[k2] = cadd(E, cmul(stw[k2], O));
-        }
-    }
 }
 
-// x pass, inverse (c2r) in place: rows of n complex (k_x < N/2) -> N reals (unnormalised).
+// x pass, inverse (c2r) in place, persistent over groups of 8 rows of `nfields` arrays.
 template <int n>
-__global__ void __launch_bounds__(256) k_fx_inv(float2* __restrict__ data, size_t fstride,
-                                                const float2* __restrict__ tw) {
-    using C = XCfg<n>;
-    using TL = typename C::TL;
-    __shared__ float2 sm[TL::SIZE];
-    __shared__ float2 stw[C::N];
-    for (int e = threadIdx.x; e < C::N; e += C::T) stw[e] = tw[e];
-    float2* d = data + blockIdx.y * fstride + (size_t)blockIdx.x * C::WX * n;
-    for (int e = threadIdx.x; e < C::WX * n; e += C::T) sm[TL::at(e / n, e % n)] = d[e];
-    __syncthreads();
-    constexpr int H = n / 2 + 1;
-    for (int e = threadIdx.x; e < C::WX * H; e += C::T) {
-        const int line = e / H, k = e % H;
-        const float2 xk = sm[TL::at(line, k)];
-        if (k == 0) {
-            sm[TL::at(line, 0)] = make_float2(xk.x - xk.y, xk.y + xk.x);   // X0 + i X0
-            continue;
+struct FxInv {
+    static constexpr int N = 2 * n, T = XT<n>::T;
+    using St = RowStage<n, 8>;
+    static constexpr size_t SMEM = 2 * St::BYTES + TCfg<n>::TILE + sizeof(float2) * N;
+};
+
+template <int n>
+__global__ void __launch_bounds__(XT<n>::T) k_fx_inv(float2* __restrict__ data, size_t fstride,
+                                                      const float2* __restrict__ tw, int items_per_field,
+                                                      int nfields) {
+    using C = FxInv<n>;
+    constexpr int T = C::T, N = C::N;
+    extern __shared__ float4 smem4[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(smem4);
+    float2* tile = reinterpret_cast<float2*>(base + 2 * C::St::BYTES);
+    float2* stw = tile + 8 * n;
+    for (int e = threadIdx.x; e < N; e += T) stw[e] = tw[e];
+    const int nitems = items_per_field * nfields;
+    auto gptr = [&](int t) { return data + (size_t)(t / items_per_field) * fstride + (size_t)(t % items_per_field) * 8 * n; };
+    int t = blockIdx.x;
+    if (t < nitems) ld_rows_stage<n, T, 8>(base, reinterpret_cast<const unsigned char*>(gptr(t)));
+    cp_async_commit();
+    for (int it = 0; t < nitems; t += gridDim.x, ++it) {
+        float2* stg = reinterpret_cast<float2*>(base + (it & 1) * C::St::BYTES);
+        const int tn = t + gridDim.x;
+        if (tn < nitems)
+            ld_rows_stage<n, T, 8>(base + ((it + 1) & 1) * C::St::BYTES, reinterpret_cast<const unsigned char*>(gptr(tn)));
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        stage_to_tile<n, T>(tile, stg);
+        __syncthreads();
+        constexpr int H = n / 2 + 1;
+        for (int e = threadIdx.x; e < 8 * H; e += T) {
+            const int c = e & 7, k = e >> 3;
+            const float2 xk = tile[CT<n>::a2(k, c)];
+            if (k == 0) {
+                tile[CT<n>::a2(0, c)] = make_float2(xk.x - xk.y, xk.y + xk.x);   // X0 + i X0
+                continue;
+            }
+            const int k2 = n - k;
+            const float2 xk2 = tile[CT<n>::a2(k2, c)];
+            {
+                const float2 xc = cconj(xk2);
+                const float2 E = cadd(xk, xc);
+                const float2 O = cmul(csub(xk, xc), cconj(stw[k]));
+                tile[CT<n>::a2(k, c)] = make_float2(E.x - O.y, E.y + O.x);
+            }
+            if (k2 != k) {
+                const float2 xc = cconj(xk);
+                const float2 E = cadd(xk2, xc);
+                const float2 O = cmul(csub(xk2, xc), cconj(stw[k2]));
+                tile[CT<n>::a2(k2, c)] = make_float2(E.x - O.y, E.y + O.x);
+            }
         }
-        const int k2 = n - k;
-        const float2 xk2 = sm[TL::at(line, k2)];
-        {
-            const float2 xc = cconj(xk2);
-            const float2 E = cadd(xk, xc);
-            const float2 O = cmul(csub(xk, xc), cconj(stw[k]));
-            sm[TL::at(line, k)] = make_float2(E.x - O.y, E.y + O.x);
-        }
-        if (k2 != k) {
-            const float2 xc = cconj(xk);
-            const float2 E = cadd(xk2, xc);
-            const float2 O = cmul(csub(xk2, xc), cconj(stw[k2]));
-            sm[TL::at(line, k2)] = make_float2(E.x - O.y, E.y + O.x);
-        }
+        __syncthreads();
+        tile_fft<n, T, +1, N>(tile, stw);
+        tile_to_rows<n, T>(tile, stg, gptr(t));
+        __syncthreads();
     }
-    __syncthreads();
-    tile_fft<n, C::WX, C::T, true, +1, C::N>(sm, stw);
-    for (int e = threadIdx.x; e < C::WX * n; e += C::T) d[e] = sm[TL::at(e / n, e % n)];
+    cp_async_wait<0>();
 }
 
-// ---------------------------------------------------------------------------------------
-// Tile I/O of the strided passes: kW consecutive complex of each of the L lines.
-template <int L, int T>
-__device__ __forceinline__ void load_cols(float2* sm, const float2* __restrict__ g, size_t stride) {
-    using TL = Tile<L, kW, false>;
-    for (int e = threadIdx.x; e < L * (kW / 2); e += T) {
-        const int pos = e / (kW / 2), c = (e % (kW / 2)) * 2;
-        const float4 v = *reinterpret_cast<const float4*>(g + (size_t)pos * stride + c);
-        sm[TL::at(c, pos)] = make_float2(v.x, v.y);
-        sm[TL::at(c + 1, pos)] = make_float2(v.z, v.w);
-    }
-}
-template <int L, int T>
-__device__ __forceinline__ void load_cols_async(float2* sm, const float2* __restrict__ g, size_t stride) {
-    using TL = Tile<L, kW, false>;
-    for (int e = threadIdx.x; e < L * kW; e += T) {
-        const int pos = e / kW, c = e % kW;
-        cp_async8(&sm[TL::at(c, pos)], g + (size_t)pos * stride + c);
-    }
-}
-// Store out[pos][c] = (i s_c) * A[pos][c] (IMAG: multiply by i) or s_c * A[pos][c], where the
-// per-column scale s_c = scale_c(c).
-template <int L, int T, bool IMAG, typename F>
-__device__ __forceinline__ void store_cols_scaled(const float2* sm, float2* __restrict__ g, size_t stride, F scale_c) {
-    using TL = Tile<L, kW, false>;
-    for (int e = threadIdx.x; e < L * (kW / 2); e += T) {
-        const int pos = e / (kW / 2), c = (e % (kW / 2)) * 2;
-        const float2 a = sm[TL::at(c, pos)], b = sm[TL::at(c + 1, pos)];
-        const float sa = scale_c(c), sb = scale_c(c + 1);
-        float4 v;
-        if constexpr (IMAG)
-            v = make_float4(-sa * a.y, sa * a.x, -sb * b.y, sb * b.x);
-        else
-            v = make_float4(sa * a.x, sa * a.y, sb * b.x, sb * b.y);
-        *reinterpret_cast<float4*>(g + (size_t)pos * stride + c) = v;
-    }
-}
-template <int L, int T>
-__device__ __forceinline__ void store_cols(const float2* sm, float2* __restrict__ g, size_t stride) {
-    store_cols_scaled<L, T, false>(sm, g, stride, [](int) { return 1.0f; });
-}
-
+// ---------------------------------------------------------------------------------------------
 // y pass in place, persistent over all column tiles of `nfields` arrays.
+template <int L>
+struct Fy {
+    static constexpr int T = TCfg<L>::T;
+    static constexpr size_t SMEM = 2 * TCfg<L>::TILE + sizeof(float2) * L;
+};
+
 template <int L, int S>
-__global__ void __launch_bounds__(YCfg<L>::T) k_fy(float2* __restrict__ data, size_t fstride,
+__global__ void __launch_bounds__(TCfg<L>::T) k_fy(float2* __restrict__ data, size_t fstride,
                                                     const float2* __restrict__ tw, int nfields) {
     constexpr int n = L / 2;
-    constexpr int T = YCfg<L>::T;
-    constexpr int NG = n / kW;           // column groups per plane
+    constexpr int T = Fy<L>::T;
+    constexpr int NG = n / 8;            // column groups per plane
     constexpr int TPF = NG * L;          // tiles per field
-    using TL = Tile<L, kW, false>;
-    extern __shared__ float2 sm[];
-    float2* stw = sm + 2 * TL::SIZE;
+    extern __shared__ float4 smem4[];
+    float2* bufs = reinterpret_cast<float2*>(smem4);
+    float2* stw = bufs + 2 * 8 * L;
     for (int e = threadIdx.x; e < L; e += T) stw[e] = tw[e];
     const int total = TPF * nfields;
     auto tile_ptr = [&](int t) {
         const int f = t / TPF, r = t % TPF;
-        return data + (size_t)f * fstride + (size_t)(r / NG) * L * n + (r % NG) * kW;
+        return data + (size_t)f * fstride + (size_t)(r / NG) * L * n + (r % NG) * 8;
     };
     int t = blockIdx.x;
-    if (t < total) load_cols_async<L, T>(sm, tile_ptr(t), n);
+    if (t < total) ld_cols<L, T>(bufs, tile_ptr(t), n);
     cp_async_commit();
     for (int it = 0; t < total; t += gridDim.x, ++it) {
-        float2* cur = sm + (it & 1) * TL::SIZE;
-        float2* nxt = sm + ((it + 1) & 1) * TL::SIZE;
+        float2* cur = bufs + (it & 1) * 8 * L;
         const int tn = t + gridDim.x;
-        if (tn < total) load_cols_async<L, T>(nxt, tile_ptr(tn), n);
+        if (tn < total) ld_cols<L, T>(bufs + ((it + 1) & 1) * 8 * L, tile_ptr(tn), n);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        tile_fft<L, kW, T, false, S, L>(cur, stw);
-        store_cols<L, T>(cur, tile_ptr(t), n);
+        tile_fft<L, T, S, L>(cur, stw);
+        st_cols<L, T>(cur, tile_ptr(t), n);
         __syncthreads();
     }
     cp_async_wait<0>();
@@ -242,6 +323,12 @@ struct ZCfg {
     static constexpr int NBUF = (PREFETCH ? 2 : 1) + (NBASE > 1 ? NBASE - 1 : 0);
 };
 
+template <int L, int MODE>
+struct Fz {
+    static constexpr int T = TCfg<L>::T;
+    static constexpr size_t BASE_SMEM = ZCfg<MODE>::NBUF * TCfg<L>::TILE + sizeof(float2) * L;
+};
+
 // z pass with the spectral operator fused, persistent over the (k_y, column group) tiles.
 //
 // Every output of a mode is a column scale (1, i k_x, i k_y, k_x^2, ...) times the inverse z
@@ -252,19 +339,20 @@ struct ZCfg {
 //   LPT1:   Psi1 as force (d = 0); phi_xx = k_x^2 A, phi_yy = k_y^2 A, phi_zz = C, phi_xy = k_x k_y A,
 //           phi_xz = k_x B, phi_yz = k_y B                      (C = IFFT_z k_z^2 phi)
 template <int L, int MODE>
-__global__ void __launch_bounds__(YCfg<L>::T) k_fz(float2* __restrict__ in, ZOut out,
+__global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut out,
                                                     const float2* __restrict__ tw,
                                                     const float* __restrict__ sinc2, int deconv,
                                                     float gnorm, PowerArgs pw) {
     constexpr int n = L / 2;
-    constexpr int T = YCfg<L>::T;
-    constexpr int NG = n / kW;
+    constexpr int T = TCfg<L>::T;
+    constexpr int NG = n / 8;
     constexpr int NTILE = NG * L;
-    using TL = Tile<L, kW, false>;
+    constexpr int TS = 8 * L;            // tile size (float2)
     using Z = ZCfg<MODE>;
-    extern __shared__ float2 sm[];
-    float2* aux = sm + (Z::PREFETCH ? 2 : 1) * TL::SIZE;   // bases B, C
-    float2* stw = sm + Z::NBUF * TL::SIZE;
+    extern __shared__ float4 smem4[];
+    float2* sm = reinterpret_cast<float2*>(smem4);
+    float2* aux = sm + (Z::PREFETCH ? 2 : 1) * TS;   // bases B, C
+    float2* stw = sm + Z::NBUF * TS;
     for (int e = threadIdx.x; e < L; e += T) stw[e] = tw[e];
     double* ksum = reinterpret_cast<double*>(stw + L);
     double* psum = ksum + pw.nbins;
@@ -278,37 +366,38 @@ __global__ void __launch_bounds__(YCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
     }
     const float kf = 6.283185307179586f / (float)L;
     const size_t stride = (size_t)L * n;
-    auto tile_base = [&](int t) { return (size_t)(t / NG) * n + (t % NG) * kW; };
+    auto tile_base = [&](int t) { return (size_t)(t / NG) * n + (t % NG) * 8; };
 
     int t = blockIdx.x;
     if constexpr (Z::PREFETCH) {
-        if (t < NTILE) load_cols_async<L, T>(sm, in + tile_base(t), stride);
+        if (t < NTILE) ld_cols<L, T>(sm, in + tile_base(t), stride);
         cp_async_commit();
     }
     for (int it = 0; t < NTILE; t += gridDim.x, ++it) {
         float2* cur = sm;
         if constexpr (Z::PREFETCH) {
-            cur = sm + (it & 1) * TL::SIZE;
-            float2* nxt = sm + ((it + 1) & 1) * TL::SIZE;
+            cur = sm + (it & 1) * TS;
             const int tn = t + gridDim.x;
-            if (tn < NTILE) load_cols_async<L, T>(nxt, in + tile_base(tn), stride);
+            if (tn < NTILE) ld_cols<L, T>(sm + ((it + 1) & 1) * TS, in + tile_base(tn), stride);
             cp_async_commit();
             cp_async_wait<1>();
         } else {
-            load_cols<L, T>(cur, in + tile_base(t), stride);
+            ld_cols<L, T>(cur, in + tile_base(t), stride);
+            cp_async_commit();
+            cp_async_wait<0>();
         }
         __syncthreads();
-        if constexpr (Z::FWD) tile_fft<L, kW, T, false, -1, L>(cur, stw);
+        if constexpr (Z::FWD) tile_fft<L, T, -1, L>(cur, stw);
 
-        const int ky = t / NG, kx0 = (t % NG) * kW;
+        const int ky = t / NG, kx0 = (t % NG) * 8;
         const int ny = signed_bin(ky, L);
         const bool nyq_y = (ky == L / 2);
         const size_t base = tile_base(t);
 
         if constexpr (MODE == Z_POWER) {
             // Each thread bins a run of consecutive z of one column, flushing when the bin changes.
-            constexpr int PER = L * kW / T;
-            const int c = threadIdx.x % kW, z0 = (threadIdx.x / kW) * PER;
+            constexpr int PER = L * 8 / T;
+            const int c = threadIdx.x % 8, z0 = (threadIdx.x / 8) * PER;
             const int nx = kx0 + c;
             int rb = -1;
             double rp = 0.0, rk = 0.0;   // FP64 sums of FP32 per-mode values
@@ -333,7 +422,7 @@ __global__ void __launch_bounds__(YCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
                         rk = 0.0;
                         rc = 0;
                     }
-                    const float2 v = cur[TL::at(c, z)];
+                    const float2 v = cur[CT<L>::a2(z, c)];
                     const float w = sinc2[nx] * sinc2[ky] * sinc2[z];
                     rp += (double)(mult * (v.x * v.x + v.y * v.y) * pw.pnorm / (w * w));
                     rk += (double)mult * pw.kmag_of_n2[n2];
@@ -348,45 +437,53 @@ __global__ void __launch_bounds__(YCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
             __syncthreads();
             continue;
         } else {
-            // bases
-            for (int e = threadIdx.x; e < L * kW; e += T) {
-                const int z = e / kW, c = e % kW;
-                const int nx = kx0 + c, nz = signed_bin(z, L);
-                const int i = TL::at(c, z);
-                float g = 0.0f;
-                if (!nyq_y && z != L / 2 && (nx | ny | nz) != 0) {
-                    const float k2 = kf * kf * (float)(nx * nx + ny * ny + nz * nz);
-                    float w = 1.0f;
-                    if (MODE == Z_FORCE && deconv) {
-                        w = sinc2[nx] * sinc2[ky] * sinc2[z];
-                        if (deconv == 2) w *= w;
+            // bases: A = g v, B = k_z A (, C = k_z^2 A), g = gnorm / (k^2 [W^d]), 0 on excluded modes
+            float4* c4 = reinterpret_cast<float4*>(cur);
+            float4* a4p = reinterpret_cast<float4*>(aux);
+            for (int e = threadIdx.x; e < L * 4; e += T) {
+                const int z = e >> 2, q = e & 3;
+                const int nz = signed_bin(z, L);
+                const int i4 = CT<L>::a4(z, q);
+                float g[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int nx = kx0 + 2 * q + h;
+                    g[h] = 0.0f;
+                    if (!nyq_y && z != L / 2 && (nx | ny | nz) != 0) {
+                        const float k2 = kf * kf * (float)(nx * nx + ny * ny + nz * nz);
+                        float w = 1.0f;
+                        if (MODE == Z_FORCE && deconv) {
+                            w = sinc2[nx] * sinc2[ky] * sinc2[z];
+                            if (deconv == 2) w *= w;
+                        }
+                        g[h] = gnorm / (k2 * w);
                     }
-                    g = gnorm / (k2 * w);
                 }
-                const float2 v = cur[i];
-                const float2 a = make_float2(g * v.x, g * v.y);
+                const float4 v = c4[i4];
+                const float4 a = make_float4(g[0] * v.x, g[0] * v.y, g[1] * v.z, g[1] * v.w);
                 const float kz = kf * (float)nz;
-                cur[i] = a;
-                aux[i] = make_float2(kz * a.x, kz * a.y);
-                if constexpr (Z::NBASE == 3) aux[TL::SIZE + i] = make_float2(kz * kz * a.x, kz * kz * a.y);
+                c4[i4] = a;
+                a4p[i4] = make_float4(kz * a.x, kz * a.y, kz * a.z, kz * a.w);
+                if constexpr (Z::NBASE == 3)
+                    a4p[TS / 2 + i4] = make_float4(kz * kz * a.x, kz * kz * a.y, kz * kz * a.z, kz * kz * a.w);
             }
             __syncthreads();
-            tile_fft<L, kW, T, false, +1, L>(cur, stw);
-            tile_fft<L, kW, T, false, +1, L>(aux, stw);
-            if constexpr (Z::NBASE == 3) tile_fft<L, kW, T, false, +1, L>(aux + TL::SIZE, stw);
+            tile_fft<L, T, +1, L>(cur, stw);
+            tile_fft<L, T, +1, L>(aux, stw);
+            if constexpr (Z::NBASE == 3) tile_fft<L, T, +1, L>(aux + TS, stw);
             const float kyv = kf * (float)ny;
             auto kxv = [&](int c) { return kf * (float)(kx0 + c); };
             constexpr float sg = MODE == Z_LPT2 ? -1.0f : 1.0f;
-            store_cols_scaled<L, T, true>(cur, out.p[0] + base, stride, [&](int c) { return sg * kxv(c); });
-            store_cols_scaled<L, T, true>(cur, out.p[1] + base, stride, [&](int) { return sg * kyv; });
-            store_cols_scaled<L, T, true>(aux, out.p[2] + base, stride, [&](int) { return sg; });
+            st_cols_scaled<L, T, true>(cur, out.p[0] + base, stride, [&](int c) { return sg * kxv(c); });
+            st_cols_scaled<L, T, true>(cur, out.p[1] + base, stride, [&](int) { return sg * kyv; });
+            st_cols_scaled<L, T, true>(aux, out.p[2] + base, stride, [&](int) { return sg; });
             if constexpr (MODE == Z_LPT1) {
-                store_cols_scaled<L, T, false>(cur, out.p[3] + base, stride, [&](int c) { return kxv(c) * kxv(c); });
-                store_cols_scaled<L, T, false>(cur, out.p[4] + base, stride, [&](int) { return kyv * kyv; });
-                store_cols_scaled<L, T, false>(aux + TL::SIZE, out.p[5] + base, stride, [&](int) { return 1.0f; });
-                store_cols_scaled<L, T, false>(cur, out.p[6] + base, stride, [&](int c) { return kxv(c) * kyv; });
-                store_cols_scaled<L, T, false>(aux, out.p[7] + base, stride, [&](int c) { return kxv(c); });
-                store_cols_scaled<L, T, false>(aux, out.p[8] + base, stride, [&](int) { return kyv; });
+                st_cols_scaled<L, T, false>(cur, out.p[3] + base, stride, [&](int c) { return kxv(c) * kxv(c); });
+                st_cols_scaled<L, T, false>(cur, out.p[4] + base, stride, [&](int) { return kyv * kyv; });
+                st_cols_scaled<L, T, false>(aux + TS, out.p[5] + base, stride, [&](int) { return 1.0f; });
+                st_cols_scaled<L, T, false>(cur, out.p[6] + base, stride, [&](int c) { return kxv(c) * kyv; });
+                st_cols_scaled<L, T, false>(aux, out.p[7] + base, stride, [&](int c) { return kxv(c); });
+                st_cols_scaled<L, T, false>(aux, out.p[8] + base, stride, [&](int) { return kyv; });
             }
             __syncthreads();
         }
@@ -402,25 +499,6 @@ __global__ void __launch_bounds__(YCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
             }
         }
     }
-}
-
-// ---------------------------------------------------------------------------------------
-// Launch helpers (host).
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// Persistent grid: resident CTAs per SM x SMs (computed once per kernel and shared-memory size).
-template <typename K>
-static int persistent_grid(K kernel, int threads, size_t smem) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
-    if (per < 1) per = 1;
-    return per * sms;
 }
 
 #define COLAPM_FOR_MESH_SIZES(X) X(16) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384) X(512) X(1024)

@@ -1,19 +1,33 @@
 // y passes (strided columns, both directions) for every supported mesh size.
+#include "fft2.cuh"
 #include "fft_kernels.cuh"
 
 namespace colapm {
 
 template <int N, int S>
 static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
-    using C = YCfg<N>;
-    constexpr size_t smem = 2 * C::TILE_BYTES + C::TW_BYTES;
+    if constexpr (F2Has<N>::value) {
+        using K = K2<N>;
+        constexpr size_t smem = sizeof(float2) * Xch<N, K::RA>::SIZE + sizeof(Tw2);
+        static int grid2 = 0;
+        if (!grid2) {
+            cudaError_t e = set_smem(k2_fy<N, S>, smem);
+            if (e != cudaSuccess) return e;
+            grid2 = persistent_grid(k2_fy<N, S>, K::T, smem);
+        }
+        const int total = (N / 2 / 8) * N * nfields;
+        k2_fy<N, S><<<grid2 < total ? grid2 : total, K::T, smem, s>>>(data, fstride, tw, nfields);
+        return cudaGetLastError();
+    }
+    using C = Fy<N>;
+    constexpr size_t smem = C::SMEM;
     static int grid = 0;
     if (!grid) {
         cudaError_t e = set_smem(k_fy<N, S>, smem);
         if (e != cudaSuccess) return e;
         grid = persistent_grid(k_fy<N, S>, C::T, smem);
     }
-    const int total = (N / 2 / kW) * N * nfields;
+    const int total = (N / 2 / 8) * N * nfields;
     k_fy<N, S><<<grid < total ? grid : total, C::T, smem, s>>>(data, fstride, tw, nfields);
     return cudaGetLastError();
 }

@@ -1,4 +1,5 @@
 // z passes with the fused spectral operators for every supported mesh size.
+#include "fft2.cuh"
 #include "fft_kernels.cuh"
 
 namespace colapm {
@@ -6,8 +7,23 @@ namespace colapm {
 template <int N, int MODE>
 static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm,
                            PowerArgs pw, cudaStream_t s) {
-    using C = YCfg<N>;
-    const size_t smem = ZCfg<MODE>::NBUF * C::TILE_BYTES + C::TW_BYTES + (MODE == Z_POWER ? (size_t)pw.nbins * 24 : 0);
+    if constexpr (F2Has<N>::value) {
+        using Z = Z2<N, MODE>;
+        const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 : 0);
+        static size_t configured2 = 0;
+        static int grid2 = 0;
+        if (smem > configured2 || !grid2) {
+            cudaError_t e = set_smem(k2_fz<N, MODE>, smem);
+            if (e != cudaSuccess) return e;
+            configured2 = smem > configured2 ? smem : configured2;
+            grid2 = persistent_grid(k2_fz<N, MODE>, K2<N>::T, smem);
+        }
+        const int total = (N / 2 / 8) * N;
+        k2_fz<N, MODE><<<grid2 < total ? grid2 : total, K2<N>::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
+        return cudaGetLastError();
+    }
+    using C = Fz<N, MODE>;
+    const size_t smem = C::BASE_SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 : 0);
     static size_t configured = 0;
     static int grid = 0;
     if (smem > configured || !grid) {
@@ -16,7 +32,7 @@ static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* 
         configured = smem > configured ? smem : configured;
         grid = persistent_grid(k_fz<N, MODE>, C::T, smem);
     }
-    const int total = (N / 2 / kW) * N;
+    const int total = (N / 2 / 8) * N;
     k_fz<N, MODE><<<grid < total ? grid : total, C::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
     return cudaGetLastError();
 }
