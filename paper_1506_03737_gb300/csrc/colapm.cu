@@ -31,8 +31,7 @@ struct colapm_ctx {
     float* amp_p = nullptr;              // Gaussian-field amplitude per integer |n|^2 of the IC grid
     int* err = nullptr;                  // device error bits: 1 overflow, 2 bad state import
     // power-spectrum tables (grown on demand)
-    int* pw_bin = nullptr;
-    double* pw_kmag = nullptr;
+    int* pw_bin = nullptr;               // |n|^2 thresholds of the bins
     double* pw_acc = nullptr;            // ksum[nb], psum[nb], cnt[nb] (as u64)
     int pw_n2cap = 0, pw_nbcap = 0;
     int step = 0;
@@ -96,7 +95,7 @@ bool is_device_ptr(const void* p) {
 
 void free_all(colapm_ctx* c) {
     void* ptrs[] = {c->rho, c->F, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
-                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_kmag, c->pw_acc};
+                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& v : c->ev)
@@ -408,33 +407,29 @@ int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_o
     if (kmax <= 0) kmax = M_PI * c->nm / box;
     if (!(kmax > kmin)) return COLAPM_E_ARG;
     const int h = c->nm / 2, n2max = 3 * h * h;
-    // Bin of every integer |n|^2, decided in FP64 with the same expressions as the definition:
-    // |k| = (2 pi / L) sqrt(n^2), edges e_b = kmin (kmax / kmin)^(b / nbins), e_b <= |k| < e_{b+1}.
-    std::vector<int> bin(n2max + 1, -1);
-    std::vector<double> kmag(n2max + 1);
+    // Bin membership of every integer |n|^2, decided in FP64 with the same expressions as the
+    // definition: |k| = (2 pi / L) sqrt(n^2), edges e_b = kmin (kmax / kmin)^(b / nbins),
+    // e_b <= |k| < e_{b+1}. It is monotone in n^2, so it is passed to the kernels as the
+    // thresholds n2_lo[b] = smallest n^2 whose bin is >= b (|k| below e_0 counts as bin -1,
+    // |k| >= e_nbins as bin nbins).
     std::vector<double> edges(nbins + 1);
     for (int b = 0; b <= nbins; ++b) edges[b] = kmin * std::pow(kmax / kmin, (double)b / nbins);
-    for (int n2 = 0; n2 <= n2max; ++n2) {
-        const double km = kf * std::sqrt((double)n2);
-        kmag[n2] = km;
-        if (km < edges[0] || !(km < edges[nbins])) continue;
-        int lo = 0, hi = nbins;   // largest b with edges[b] <= km
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) / 2;
-            if (edges[mid] <= km) lo = mid; else hi = mid;
+    std::vector<int> lo(nbins + 1, n2max + 1);
+    {
+        int b = 0;
+        for (int n2 = 0; n2 <= n2max && b <= nbins; ++n2) {
+            const double km = kf * std::sqrt((double)n2);
+            while (b <= nbins && km >= edges[b]) lo[b++] = n2;   // first n^2 at or above edge b
         }
-        bin[n2] = lo;
     }
-    if (n2max + 1 > c->pw_n2cap) {
+    if (nbins + 1 > c->pw_n2cap) {
         if (c->pw_bin) cudaFree(c->pw_bin);
-        if (c->pw_kmag) cudaFree(c->pw_kmag);
         c->pw_bin = nullptr;
-        c->pw_kmag = nullptr;
-        if (dalloc(&c->pw_bin, (size_t)n2max + 1) != cudaSuccess || dalloc(&c->pw_kmag, (size_t)n2max + 1) != cudaSuccess) {
+        if (dalloc(&c->pw_bin, (size_t)nbins + 1) != cudaSuccess) {
             c->pw_n2cap = 0;
             return COLAPM_E_NOMEM;
         }
-        c->pw_n2cap = n2max + 1;
+        c->pw_n2cap = nbins + 1;
     }
     if (nbins > c->pw_nbcap) {
         if (c->pw_acc) cudaFree(c->pw_acc);
@@ -445,8 +440,7 @@ int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_o
         }
         c->pw_nbcap = nbins;
     }
-    CK(cudaMemcpyAsync(c->pw_bin, bin.data(), bin.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->pw_kmag, kmag.data(), kmag.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->pw_bin, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->pw_acc, 0, (size_t)3 * nbins * sizeof(double), c->stream));
     int r = deposit(c);
     if (r) return r;
@@ -455,13 +449,12 @@ int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_o
     {
         Phase ph(c, COLAPM_PHASE_POWER);
         PowerArgs pw{};
-        pw.bin_of_n2 = c->pw_bin;
-        pw.kmag_of_n2 = c->pw_kmag;
+        pw.n2_lo = c->pw_bin;
+        pw.kf = (float)kf;
         pw.ksum = c->pw_acc;
         pw.psum = c->pw_acc + nbins;
         pw.cnt = reinterpret_cast<unsigned long long*>(c->pw_acc + 2 * nbins);
         pw.nbins = nbins;
-        pw.n2max = n2max;
         const double nm = c->nm;
         pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
         CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m, 0, 1.0f, &pw,

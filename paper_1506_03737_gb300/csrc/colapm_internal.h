@@ -32,16 +32,30 @@ enum ZMode {
     Z_POWER = 3    // forward z, bin |delta|^2 / W^2
 };
 
+// Power-spectrum binning. Bin membership is decided in FP64 on the host (or once per call on
+// the device) and handed to the kernel as integer thresholds on |n|^2: a mode is in bin b when
+// n2_lo[b] <= |n|^2 < n2_lo[b + 1] (empty bins have equal thresholds); |n|^2 < n2_lo[0] or
+// >= n2_lo[nbins] is outside. Per-mode values are FP32, sums FP64.
 struct PowerArgs {
-    const int* bin_of_n2;       // bin index for integer |n|^2, -1 if outside
-    const double* kmag_of_n2;   // |k| for integer |n|^2
+    const int* n2_lo;           // [nbins + 1]
     double* ksum;               // [nbins]
     double* psum;               // [nbins]
     unsigned long long* cnt;    // [nbins]
     int nbins;
-    int n2max;
+    float kf;                   // 2 pi / L (h/Mpc)
     float pnorm;                // L^3 / N^6
 };
+
+// Bin of |n|^2 given the thresholds (binary search; -1 outside).
+__device__ __forceinline__ int power_bin(int n2, const int* lo, int nbins) {
+    if (n2 < lo[0] || n2 >= lo[nbins]) return -1;
+    int a = 0, b = nbins;
+    while (b - a > 1) {
+        const int m = (a + b) >> 1;
+        if (lo[m] <= n2) a = m; else b = m;
+    }
+    return a;
+}
 
 // --- launchers (fft_kernels_*.cu) ----------------------------------------------------------
 // Forward x pass (r2c) of N^2 rows of N reals into N^2 rows of N/2 complex (Nyquist dropped).

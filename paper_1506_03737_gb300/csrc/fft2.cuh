@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
     double* ksum = reinterpret_cast<double*>(tws + 1);
     double* psum = ksum + pw.nbins;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(psum + pw.nbins);
+    int* lo = reinterpret_cast<int*>(cnt + pw.nbins);
     load_tw2<L, L>(tws, tw, T);
     if constexpr (MODE == Z_POWER) {
         for (int b = threadIdx.x; b < pw.nbins; b += T) {
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
             psum[b] = 0.0;
             cnt[b] = 0ull;
         }
+        for (int b = threadIdx.x; b <= pw.nbins; b += T) lo[b] = pw.n2_lo[b];
     }
     __syncthreads();
     const float kf = 6.283185307179586f / (float)L;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
                     if (z == L / 2) continue;
                     const int nz = sbin(z, L);
                     const int n2 = px * px + ny * ny + nz * nz;
-                    const int b = (n2 == 0 || n2 > pw.n2max) ? -1 : pw.bin_of_n2[n2];
+                    const int b = n2 == 0 ? -1 : (rb >= 0 && n2 >= lo[rb] && n2 < lo[rb + 1]) ? rb : power_bin(n2, lo, pw.nbins);
                     if (b < 0) continue;
                     if (b != rb) {
                         if (rb >= 0) {
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
                     const float2 q = xb[Xch<L, R1>::at(pc, z)];
                     const float w = sinc2[px] * sinc2[ky] * sinc2[z];
                     rp += (double)(mult * (q.x * q.x + q.y * q.y) * pw.pnorm / (w * w));
-                    rk += (double)mult * pw.kmag_of_n2[n2];
+                    rk += (double)(mult * pw.kf * sqrtf((float)n2));
                     rc += px == 0 ? 1u : 2u;
                 }
                 if (rb >= 0) {

@@ -357,12 +357,14 @@ __global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
     double* ksum = reinterpret_cast<double*>(stw + L);
     double* psum = ksum + pw.nbins;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(psum + pw.nbins);
+    int* lo = reinterpret_cast<int*>(cnt + pw.nbins);
     if constexpr (MODE == Z_POWER) {
         for (int b = threadIdx.x; b < pw.nbins; b += T) {
             ksum[b] = 0.0;
             psum[b] = 0.0;
             cnt[b] = 0ull;
         }
+        for (int b = threadIdx.x; b <= pw.nbins; b += T) lo[b] = pw.n2_lo[b];
     }
     const float kf = 6.283185307179586f / (float)L;
     const size_t stride = (size_t)L * n;
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
                     if (z == L / 2) continue;
                     const int nz = signed_bin(z, L);
                     const int n2 = nx * nx + ny * ny + nz * nz;
-                    const int b = (n2 == 0 || n2 > pw.n2max) ? -1 : pw.bin_of_n2[n2];
+                    const int b = n2 == 0 ? -1 : (rb >= 0 && n2 >= lo[rb] && n2 < lo[rb + 1]) ? rb : power_bin(n2, lo, pw.nbins);
                     if (b < 0) continue;
                     if (b != rb) {
                         if (rb >= 0) {
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
                     const float2 v = cur[CT<L>::a2(z, c)];
                     const float w = sinc2[nx] * sinc2[ky] * sinc2[z];
                     rp += (double)(mult * (v.x * v.x + v.y * v.y) * pw.pnorm / (w * w));
-                    rk += (double)mult * pw.kmag_of_n2[n2];
+                    rk += (double)(mult * pw.kf * sqrtf((float)n2));
                     rc += nx == 0 ? 1u : 2u;
                 }
             }

@@ -9,7 +9,7 @@ static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* 
                            PowerArgs pw, cudaStream_t s) {
     if constexpr (F2Has<N>::value) {
         using Z = Z2<N, MODE>;
-        const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 : 0);
+        const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
         static size_t configured2 = 0;
         static int grid2 = 0;
         if (smem > configured2 || !grid2) {
@@ -23,7 +23,7 @@ static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* 
         return cudaGetLastError();
     }
     using C = Fz<N, MODE>;
-    const size_t smem = C::BASE_SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 : 0);
+    const size_t smem = C::BASE_SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
     static size_t configured = 0;
     static int grid = 0;
     if (smem > configured || !grid) {

@@ -20,7 +20,6 @@ namespace {
 
 constexpr int kMaxNm = COLAPM_NOALLOC_MAX_NM;
 constexpr int kMaxBins = COLAPM_NOALLOC_MAX_BINS;
-constexpr int kMaxN2 = 3 * (kMaxNm / 2) * (kMaxNm / 2);
 
 // Byte offsets of the scratch regions (each 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -29,9 +28,8 @@ constexpr size_t kSpec = align256(kRho + sizeof(unsigned long long) * kMaxNm * k
 constexpr size_t kTw = align256(kSpec + sizeof(float2) * kMaxNm * kMaxNm * kMaxNm / 2);            // float2 [nm]
 constexpr size_t kSinc = align256(kTw + sizeof(float2) * kMaxNm);                  // float [nm]
 constexpr size_t kEdges = align256(kSinc + sizeof(float) * kMaxNm);                // double [nbins + 1]
-constexpr size_t kBin = align256(kEdges + sizeof(double) * (kMaxBins + 1));        // int [n2max + 1]
-constexpr size_t kKmag = align256(kBin + sizeof(int) * (kMaxN2 + 1));              // double [n2max + 1]
-constexpr size_t kAcc = align256(kKmag + sizeof(double) * (kMaxN2 + 1));           // double [3 nbins]
+constexpr size_t kBin = align256(kEdges + sizeof(double) * (kMaxBins + 1));        // int [nbins + 1] thresholds
+constexpr size_t kAcc = align256(kBin + sizeof(int) * (kMaxBins + 1));             // double [3 nbins]
 constexpr size_t kOut = align256(kAcc + sizeof(double) * 3 * kMaxBins);            // k, P (double), n (i64)
 constexpr size_t kErr = align256(kOut + sizeof(double) * 3 * kMaxBins);            // int [4]
 constexpr size_t kBytes = align256(kErr + 4 * sizeof(int));
@@ -70,24 +68,18 @@ __global__ void k_deposit_xyz(const int* __restrict__ cell, const float* __restr
             }
 }
 
-// Bin of every integer |n|^2 in FP64: |k| = kf sqrt(n^2) (correctly rounded), largest b with
-// edges[b] <= |k|, -1 outside [edges[0], edges[nbins]).
-__global__ void k_bin_table(const double* __restrict__ edges, int nbins, double kf, int n2max, int* __restrict__ bin,
-                            double* __restrict__ kmag) {
-    const int n2 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n2 > n2max) return;
-    const double km = kf * sqrt((double)n2);
-    kmag[n2] = km;
-    int b = -1;
-    if (km >= edges[0] && km < edges[nbins]) {
-        int lo = 0, hi = nbins;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) / 2;
-            if (edges[mid] <= km) lo = mid; else hi = mid;
-        }
-        b = lo;
+// Bin thresholds in FP64: n2_lo[b] = smallest integer |n|^2 with kf sqrt(|n|^2) >= edges[b]
+// (sqrt correctly rounded), n2max + 1 if none; one thread per edge, binary search over |n|^2.
+__global__ void k_bin_thresholds(const double* __restrict__ edges, int nbins, double kf, int n2max,
+                                 int* __restrict__ lo) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbins) return;
+    int a = 0, z = n2max + 1;   // find the first n2 in [0, n2max + 1) with kf sqrt(n2) >= edges[b]
+    while (a < z) {
+        const int m = (a + z) >> 1;
+        if (kf * sqrt((double)m) >= edges[b]) z = m; else a = m + 1;
     }
-    bin[n2] = b;
+    lo[b] = a;
 }
 
 __global__ void k_finish(const double* __restrict__ acc, int nbins, double* __restrict__ out) {
@@ -151,7 +143,6 @@ extern "C" int colapm_power_noalloc(const int* cell, const float* offset, long l
     auto* sinc2 = reinterpret_cast<float*>(base + kSinc);
     auto* edges = reinterpret_cast<double*>(base + kEdges);
     auto* bin = reinterpret_cast<int*>(base + kBin);
-    auto* kmag = reinterpret_cast<double*>(base + kKmag);
     auto* acc = reinterpret_cast<double*>(base + kAcc);
     auto* out = reinterpret_cast<double*>(base + kOut);
     auto* err = reinterpret_cast<int*>(base + kErr);
@@ -182,7 +173,7 @@ extern "C" int colapm_power_noalloc(const int* cell, const float* offset, long l
     NCK(cudaMemsetAsync(rho, 0, sizeof(unsigned long long) * nm3, s));
     NCK(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * nbins, s));
     NCK(cudaMemsetAsync(err, 0, 4 * sizeof(int), s));
-    k_bin_table<<<(n2max + 256) / 256, 256, 0, s>>>(edges, nbins, kf, n2max, bin, kmag);
+    k_bin_thresholds<<<(nbins + 128) / 128, 128, 0, s>>>(edges, nbins, kf, n2max, bin);
     NCK(cudaGetLastError());
     k_deposit_xyz<<<(unsigned)((n_particles + 255) / 256), 256, 0, s>>>(cell, offset, n_particles, nm, rho, err);
     NCK(cudaGetLastError());
@@ -190,13 +181,12 @@ extern "C" int colapm_power_noalloc(const int* cell, const float* offset, long l
     NCK(launch_fx_fwd_i64(nm, rho, spec, tw, (float)(ratio * std::ldexp(1.0, -45)), err, s));
     NCK(launch_fy(nm, -1, spec, 0, 1, tw, s));
     PowerArgs pw{};
-    pw.bin_of_n2 = bin;
-    pw.kmag_of_n2 = kmag;
+    pw.n2_lo = bin;
+    pw.kf = (float)kf;
     pw.ksum = acc;
     pw.psum = acc + nbins;
     pw.cnt = reinterpret_cast<unsigned long long*>(acc + 2 * nbins);
     pw.nbins = nbins;
-    pw.n2max = n2max;
     pw.pnorm = (float)(box * box * box / ((double)nm3 * (double)nm3));
     NCK(launch_fz(nm, Z_POWER, spec, ZOut{}, tw, sinc2, 0, 1.0f, &pw, s));
     k_finish<<<(nbins + 127) / 128, 128, 0, s>>>(acc, nbins, out);

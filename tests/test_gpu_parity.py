@@ -201,7 +201,7 @@ def test_full_run_cola_32p_64m(C):
         assert np.array_equal(nmodes, nr)
         ok = nr > 0
         assert np.nanmax(np.abs(pk[ok] / pr[ok] - 1)) < 1e-3
-        assert np.nanmax(np.abs(k[ok] / kr[ok] - 1)) < 1e-12
+        assert np.nanmax(np.abs(k[ok] / kr[ok] - 1)) < 1e-6    # per-mode |k| in FP32, sums in FP64
     finally:
         s.close()
 
