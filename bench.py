@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--workload", default="cola_512p_1024m_1024mpc")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -169,6 +170,40 @@ def run_reference(args, rank, world):
 
 
 # --- GPU side ---------------------------------------------------------------------------------
+
+def batch_params(C, base_seed=1000):
+    """64 uneven mocks: N_p = 64 + 32 (r mod 5), N_m = 2 N_p, L = 128 + 96 (r mod 5) Mpc/h, 10 steps."""
+    out = []
+    for r in range(64):
+        k = r % 5
+        npp = 64 + 32 * k
+        out.append(C.default_params(np=npp, nm=2 * npp, box=128.0 + 96.0 * k, seed=base_seed + r,
+                                    **{x: workloads.COSMO[x] for x in ("omega_m", "h", "n_s", "sigma8")}))
+    return out
+
+
+def run_batch(C, stream, rank, args):
+    """Mocks/hour of the 64-mock uneven batch: one CUDA graph per batch, replayed with new seeds."""
+    params = batch_params(C)
+    ups = sum(p.np ** 3 * p.n_steps for p in params)
+    b = C.colapm_batch_create(params, nstreams=0, stream=stream.cuda_stream)
+    try:
+        t0 = time.perf_counter()
+        C.colapm_batch_run(b, 64, 100, seeds=[7000 + 64 * rank + i for i in range(64)])   # capture + stream choice
+        setup = time.perf_counter() - t0
+        reps = 2
+        t0 = time.perf_counter()
+        for rep in range(reps):
+            C.colapm_batch_run(b, 64, 100, seeds=[9000 + 1000 * rep + 64 * rank + i for i in range(64)])
+        secs = (time.perf_counter() - t0) / reps
+        return {"workload": "64 mocks, N_p = 64..192 (step 32), N_m = 2 N_p, L = 128..512 Mpc/h, 10 COLA steps, "
+                            "2LPT ICs + 100-bin P(k) each; one CUDA graph, new seeds per replay",
+                "mocks_per_hour": 64 * 3600.0 / secs, "ms_per_batch": 1e3 * secs,
+                "particle_updates_per_s": ups / secs, "worker_streams": C.colapm_batch_streams(b),
+                "first_run_s_incl_capture_and_tuning": setup}
+    finally:
+        C.colapm_batch_destroy(b)
+
 
 def main():
     args = parse()
@@ -297,9 +332,11 @@ def main():
     line["cola_step_roofline_frac"] = alg_step / (step_ms / 1e3) / 1e9 / hbm
     if e2e:
         line["e2e"] = e2e
+    C.colapm_destroy(ctx)
+    if not args.no_batch:
+        line["batch"] = run_batch(C, stream, rank, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-    C.colapm_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -182,6 +182,37 @@ int colapm_get_timing(colapm_ctx* ctx, double* ms, long long* launches);
 /* Number of CUDA kernels this context has launched so far (memsets and copies excluded). */
 long long colapm_kernel_launches(const colapm_ctx* ctx);
 
+/* ---- autotuning ------------------------------------------------------------------------- */
+/* Time the candidate configurations of this context on its current state -- the FFT engine
+ * (two-stage register FFT or shared-memory Stockham, where both exist) and the block size of
+ * the particle kernels (128, 256, 512) -- keep the fastest, and remember it for later contexts
+ * with the same (np, nm) in this process. The particle state and step counter are restored.
+ * Requires initial conditions (COLAPM_E_STATE). Synchronises. `choice` (may be NULL) receives
+ * {two_stage (0/1), block}. */
+int colapm_autotune(colapm_ctx* ctx, int* choice);
+
+/* ---- batched mocks (many independent realisations of uneven sizes) ----------------------- */
+typedef struct colapm_batch colapm_batch;   /* opaque; owns its contexts and graph */
+
+/* Create one context per entry of ps[0..n-1] (any mix of sizes), spread over `nstreams` worker
+ * streams (nstreams <= 0: choose by timing 1, 2, 4 and 8 at the first run). The batch captures
+ * and launches on streams of its own; each run first waits for the caller's `stream`.
+ * Errors as colapm_create; everything created so far is freed on failure. */
+int colapm_batch_create(int n, const colapm_params* ps, int nstreams, void* stream, colapm_batch** out);
+
+/* Run every mock: 2LPT initial conditions from seeds[i] (host array of n seeds; NULL: the seeds
+ * in ps), all n_steps COLA steps, and the P(k) of each mock in nbins bins (kmin/kmax <= 0: the
+ * per-mock defaults of colapm_power). The whole batch is captured once into a CUDA graph (per
+ * nbins/kmin/kmax) and replayed; seeds reach the graph through a pinned buffer, so each run is
+ * a new set of realisations. Outputs are host arrays of n * nbins (mock-major). Synchronises. */
+int colapm_batch_run(colapm_batch* b, const unsigned long long* seeds, int nbins, double kmin, double kmax,
+                     double* k_out, double* p_out, long long* nmodes_out);
+
+/* Worker streams in use (after the first run when chosen automatically). */
+int colapm_batch_streams(const colapm_batch* b);
+
+void colapm_batch_destroy(colapm_batch* b);
+
 /* Power spectrum of caller-owned particle positions without any allocation.
  *
  * The paper has no counterpart: this is a library convenience. It is for callers that cannot

@@ -64,6 +64,11 @@ def _load():
         "colapm_get_timing": (I, [P, P, P]),
         "colapm_strerror": (ctypes.c_char_p, [I]),
         "colapm_power_noalloc": (I, [P, P, ctypes.c_longlong, I, D, I, D, D, P, P, P, P]),
+        "colapm_autotune": (I, [P, P]),
+        "colapm_batch_create": (I, [I, P, I, P, ctypes.POINTER(P)]),
+        "colapm_batch_run": (I, [P, P, I, D, D, P, P, P]),
+        "colapm_batch_streams": (I, [P]),
+        "colapm_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -217,6 +222,37 @@ def colapm_power_noalloc(cell, offset, n_particles, nm, box, nbins, kmin=0.0, km
                                     _ptr(p_out), _ptr(n_out), ctypes.c_void_p(stream or None)),
            "colapm_power_noalloc")
     return k_out, p_out, n_out
+
+
+def colapm_autotune(ctx):
+    choice = np.zeros(2, dtype=np.int32)
+    _check(LIB.colapm_autotune(ctx, _ptr(choice)), "colapm_autotune")
+    return {"two_stage": bool(choice[0]), "block": int(choice[1])}
+
+
+def colapm_batch_create(params_list, nstreams=0, stream=0):
+    arr = (Params * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    _check(LIB.colapm_batch_create(len(params_list), ctypes.cast(arr, ctypes.c_void_p), nstreams,
+                                   ctypes.c_void_p(stream or None), ctypes.byref(b)), "colapm_batch_create")
+    return b
+
+
+def colapm_batch_run(b, n, nbins, seeds=None, kmin=0.0, kmax=0.0):
+    k = np.empty((n, nbins))
+    p = np.empty((n, nbins))
+    cnt = np.empty((n, nbins), dtype=np.int64)
+    sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+    _check(LIB.colapm_batch_run(b, _ptr(sd), nbins, kmin, kmax, _ptr(k), _ptr(p), _ptr(cnt)), "colapm_batch_run")
+    return k, p, cnt
+
+
+def colapm_batch_streams(b):
+    return LIB.colapm_batch_streams(b)
+
+
+def colapm_batch_destroy(b):
+    LIB.colapm_batch_destroy(b)
 
 
 def colapm_set_timing(ctx, on=True):

@@ -2,6 +2,8 @@
 // COLA / PM step loop, finalisation, power spectrum, state I/O and phase timing.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -34,6 +36,10 @@ struct colapm_ctx {
     int* pw_bin = nullptr;               // |n|^2 thresholds of the bins
     double* pw_acc = nullptr;            // ksum[nb], psum[nb], cnt[nb] (as u64)
     int pw_n2cap = 0, pw_nbcap = 0;
+    unsigned long long* d_seed = nullptr;          // device seed of the Gaussian field
+    const unsigned long long* seed_src = nullptr;  // the seed the ICs read (own, or a batch slot)
+    bool two_stage = true;               // FFT engine for 256/512/1024 lines (autotuned)
+    int block = 256;                     // particle-kernel block size (autotuned)
     int step = 0;
     long long launches = 0;              // kernels launched by this context
     bool has_ics = false, finalized = false;
@@ -95,7 +101,7 @@ bool is_device_ptr(const void* p) {
 
 void free_all(colapm_ctx* c) {
     void* ptrs[] = {c->rho, c->F, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
-                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc};
+                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& v : c->ev)
@@ -133,7 +139,7 @@ int copy_out(colapm_ctx* c, void* dst, const void* src, size_t bytes) {
 int deposit(colapm_ctx* c) {
     Phase ph(c, COLAPM_PHASE_DEPOSIT);
     CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
-    CKL(launch_deposit(c->pos, c->np3, c->nm, c->rho, c->stream));
+    CKL(launch_deposit(c->pos, c->np3, c->nm, c->rho, c->stream, c->block));
     return COLAPM_OK;
 }
 
@@ -146,8 +152,8 @@ float density_scale(const colapm_ctx* c) {
 int density_xy(colapm_ctx* c) {
     Phase ph(c, COLAPM_PHASE_FFT_FWD);
     float2* d = reinterpret_cast<float2*>(c->F);
-    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream));
-    CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream));
+    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, c->two_stage));
+    CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream, c->two_stage));
     return COLAPM_OK;
 }
 
@@ -166,12 +172,12 @@ int compute_force(colapm_ctx* c) {
         out.p[1] = d + fs;
         out.p[2] = d + 2 * fs;
         const float gnorm = (float)(1.0 / ((double)c->nm * c->nm * c->nm));
-        CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream));
+        CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream, c->two_stage));
     }
     {
         Phase ph(c, COLAPM_PHASE_FFT_INV);
-        CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream));
-        CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream));
+        CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage));
+        CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage));
     }
     return COLAPM_OK;
 }
@@ -274,7 +280,7 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
               dalloc(&c->scratch, 9 * c->np3) == cudaSuccess && dalloc(&c->tw_m, (size_t)c->nm) == cudaSuccess &&
               dalloc(&c->tw_p, (size_t)c->np) == cudaSuccess && dalloc(&c->sinc2_m, (size_t)c->nm) == cudaSuccess &&
               dalloc(&c->amp_p, (size_t)3 * (c->np / 2) * (c->np / 2) + 1) == cudaSuccess &&
-              dalloc(&c->err, 4) == cudaSuccess;
+              dalloc(&c->err, 4) == cudaSuccess && dalloc(&c->d_seed, 1) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -307,6 +313,7 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
         delete c;
         return COLAPM_E_CUDA;
     }
+    c->seed_src = c->d_seed;
     *out = c;
     return COLAPM_OK;
 }
@@ -328,24 +335,25 @@ int colapm_make_ics(colapm_ctx* c) {
     float2* p1 = reinterpret_cast<float2*>(c->psi1);
     float2* p2 = reinterpret_cast<float2*>(c->psi2);
     const float gnorm = (float)(1.0 / ((double)np * np * np));
-    CKL(launch_gaussian_field(np, c->prm.seed, c->amp_p, dk, c->stream));
+    if (c->seed_src == c->d_seed) CKL(launch_set_u64(c->d_seed, c->prm.seed, c->stream));
+    CKL(launch_gaussian_field(np, c->seed_src, c->amp_p, dk, c->stream));
     ZOut o1{};
     for (int j = 0; j < 3; ++j) o1.p[j] = p1 + j * hs;
     for (int j = 0; j < 6; ++j) o1.p[3 + j] = phi + j * hs;
-    CKL(launch_fz(np, Z_LPT1, dk, o1, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream));
-    CKL(launch_fy(np, +1, p1, hs, 3, c->tw_p, c->stream));
-    CKL(launch_fy(np, +1, phi, hs, 6, c->tw_p, c->stream));
-    CKL(launch_fx_inv(np, p1, hs, 3, c->tw_p, c->stream));
-    CKL(launch_fx_inv(np, phi, hs, 6, c->tw_p, c->stream));
+    CKL(launch_fz(np, Z_LPT1, dk, o1, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream, c->two_stage));
+    CKL(launch_fy(np, +1, p1, hs, 3, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fy(np, +1, phi, hs, 6, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fx_inv(np, p1, hs, 3, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fx_inv(np, phi, hs, 6, c->tw_p, c->stream, c->two_stage));
     // 2LPT: S from the six phi_ij, then Psi2 = -i k S_k / k^2.
     CKL(launch_lpt2_source(c->scratch + np3, np3, c->scratch, c->stream));
-    CKL(launch_fx_fwd_f32(np, c->scratch, phi, c->tw_p, c->stream));
-    CKL(launch_fy(np, -1, phi, 0, 1, c->tw_p, c->stream));
+    CKL(launch_fx_fwd_f32(np, c->scratch, phi, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fy(np, -1, phi, 0, 1, c->tw_p, c->stream, c->two_stage));
     ZOut o2{};
     for (int j = 0; j < 3; ++j) o2.p[j] = p2 + j * hs;
-    CKL(launch_fz(np, Z_LPT2, phi, o2, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream));
-    CKL(launch_fy(np, +1, p2, hs, 3, c->tw_p, c->stream));
-    CKL(launch_fx_inv(np, p2, hs, 3, c->tw_p, c->stream));
+    CKL(launch_fz(np, Z_LPT2, phi, o2, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream, c->two_stage));
+    CKL(launch_fy(np, +1, p2, hs, 3, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fx_inv(np, p2, hs, 3, c->tw_p, c->stream, c->two_stage));
     return place_particles(c, (float)c->nm / np);
 }
 
@@ -370,7 +378,7 @@ int colapm_step(colapm_ctx* c, int k) {
         if (r) return r;
         Phase ph(c, COLAPM_PHASE_GATHER);
         CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, coef_for(c, c->step), 1,
-                                    c->stream));
+                                    c->stream, c->block));
         ++c->step;
     }
     return COLAPM_OK;
@@ -391,27 +399,28 @@ int colapm_finalize(colapm_ctx* c) {
     }
     {
         Phase ph(c, COLAPM_PHASE_GATHER);
-        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, k, 0, c->stream));
+        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, k, 0, c->stream, c->block));
     }
     if (c->prm.cola) CKL(launch_add_lpt_momentum(c->mom, c->psi1, c->psi2, c->np3, (float)g.p1, (float)g.p2, c->stream));
     c->finalized = true;
     return COLAPM_OK;
 }
 
-int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_out, double* p_out,
-                 long long* nmodes_out) {
-    if (!c || nbins < 1 || nbins > 4096 || !k_out || !p_out || !nmodes_out) return COLAPM_E_ARG;
-    if (!c->has_ics) return COLAPM_E_STATE;
+}  // extern "C"
+
+namespace {
+
+// Upload the |n|^2 thresholds of the P(k) bins (§7.1 binning; see PowerArgs) and size the
+// accumulators. Bin membership of every integer |n|^2 is decided in FP64 with the same
+// expressions as the definition: |k| = (2 pi / L) sqrt(n^2), e_b = kmin (kmax / kmin)^(b / nbins),
+// e_b <= |k| < e_{b+1}; it is monotone in n^2, so n2_lo[b] = the smallest n^2 with |k| >= e_b.
+int power_prepare(colapm_ctx* c, int nbins, double kmin, double kmax) {
+    if (nbins < 1 || nbins > 4096) return COLAPM_E_ARG;
     const double box = c->prm.box, kf = 2.0 * M_PI / box;
     if (kmin <= 0) kmin = kf;
     if (kmax <= 0) kmax = M_PI * c->nm / box;
     if (!(kmax > kmin)) return COLAPM_E_ARG;
     const int h = c->nm / 2, n2max = 3 * h * h;
-    // Bin membership of every integer |n|^2, decided in FP64 with the same expressions as the
-    // definition: |k| = (2 pi / L) sqrt(n^2), edges e_b = kmin (kmax / kmin)^(b / nbins),
-    // e_b <= |k| < e_{b+1}. It is monotone in n^2, so it is passed to the kernels as the
-    // thresholds n2_lo[b] = smallest n^2 whose bin is >= b (|k| below e_0 counts as bin -1,
-    // |k| >= e_nbins as bin nbins).
     std::vector<double> edges(nbins + 1);
     for (int b = 0; b <= nbins; ++b) edges[b] = kmin * std::pow(kmax / kmin, (double)b / nbins);
     std::vector<int> lo(nbins + 1, n2max + 1);
@@ -441,31 +450,35 @@ int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_o
         c->pw_nbcap = nbins;
     }
     CK(cudaMemcpyAsync(c->pw_bin, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return COLAPM_OK;
+}
+
+// Deposit, forward transform and bin into the device accumulators (no host synchronisation).
+int power_enqueue(colapm_ctx* c, int nbins) {
+    const double box = c->prm.box;
     CK(cudaMemsetAsync(c->pw_acc, 0, (size_t)3 * nbins * sizeof(double), c->stream));
     int r = deposit(c);
     if (r) return r;
     r = density_xy(c);
     if (r) return r;
-    {
-        Phase ph(c, COLAPM_PHASE_POWER);
-        PowerArgs pw{};
-        pw.n2_lo = c->pw_bin;
-        pw.kf = (float)kf;
-        pw.ksum = c->pw_acc;
-        pw.psum = c->pw_acc + nbins;
-        pw.cnt = reinterpret_cast<unsigned long long*>(c->pw_acc + 2 * nbins);
-        pw.nbins = nbins;
-        const double nm = c->nm;
-        pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
-        CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m, 0, 1.0f, &pw,
-                     c->stream));
-    }
-    std::vector<double> acc(3 * nbins);
-    CK(cudaMemcpyAsync(acc.data(), c->pw_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    r = pending_error(c);   // synchronises
-    if (r) return r;
-    std::vector<double> ko(nbins), po(nbins);
-    std::vector<long long> no(nbins);
+    Phase ph(c, COLAPM_PHASE_POWER);
+    PowerArgs pw{};
+    pw.n2_lo = c->pw_bin;
+    pw.kf = (float)(2.0 * M_PI / box);
+    pw.ksum = c->pw_acc;
+    pw.psum = c->pw_acc + nbins;
+    pw.cnt = reinterpret_cast<unsigned long long*>(c->pw_acc + 2 * nbins);
+    pw.nbins = nbins;
+    const double nm = c->nm;
+    pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
+    CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m, 0, 1.0f, &pw,
+                  c->stream, c->two_stage));
+    return COLAPM_OK;
+}
+
+// Means per bin from the accumulators (ksum, psum, cnt as u64).
+void power_finish(const double* acc, int nbins, double* ko, double* po, long long* no) {
     for (int b = 0; b < nbins; ++b) {
         unsigned long long cnt;
         std::memcpy(&cnt, &acc[2 * nbins + b], sizeof(cnt));
@@ -473,6 +486,27 @@ int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_o
         ko[b] = cnt ? acc[b] / (double)cnt : NAN;
         po[b] = cnt ? acc[nbins + b] / (double)cnt : NAN;
     }
+}
+
+}  // namespace
+
+extern "C" {
+
+int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_out, double* p_out,
+                 long long* nmodes_out) {
+    if (!c || !k_out || !p_out || !nmodes_out) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    int r = power_prepare(c, nbins, kmin, kmax);
+    if (r) return r;
+    r = power_enqueue(c, nbins);
+    if (r) return r;
+    std::vector<double> acc(3 * nbins);
+    CK(cudaMemcpyAsync(acc.data(), c->pw_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    r = pending_error(c);   // synchronises
+    if (r) return r;
+    std::vector<double> ko(nbins), po(nbins);
+    std::vector<long long> no(nbins);
+    power_finish(acc.data(), nbins, ko.data(), po.data(), no.data());
     CK(cudaMemcpyAsync(k_out, ko.data(), nbins * sizeof(double), cudaMemcpyDefault, c->stream));
     CK(cudaMemcpyAsync(p_out, po.data(), nbins * sizeof(double), cudaMemcpyDefault, c->stream));
     CK(cudaMemcpyAsync(nmodes_out, no.data(), nbins * sizeof(long long), cudaMemcpyDefault, c->stream));
@@ -566,7 +600,8 @@ int colapm_get_lpt(colapm_ctx* c, float* psi1, float* psi2) {
 
 int colapm_get_gaussian_field(colapm_ctx* c, float* dk) {
     if (!c || !dk) return COLAPM_E_ARG;
-    CKL(launch_gaussian_field(c->np, c->prm.seed, c->amp_p, reinterpret_cast<float2*>(c->scratch), c->stream));
+    CKL(launch_set_u64(c->d_seed, c->prm.seed, c->stream));
+    CKL(launch_gaussian_field(c->np, c->d_seed, c->amp_p, reinterpret_cast<float2*>(c->scratch), c->stream));
     copy_out(c, dk, c->scratch, c->np3 * sizeof(float));
     return pending_error(c);
 }
@@ -660,6 +695,299 @@ int colapm_get_timing(colapm_ctx* c, double* ms, long long* launches) {
         c->ev[p].clear();
     }
     return COLAPM_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Autotuning: FFT engine and particle-kernel block size, timed on the context's own state.
+
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, std::pair<bool, int>> g_tuned;   // (np, nm) -> (two_stage, block)
+
+int colapm_autotune(colapm_ctx* c, int* choice) {
+    if (!c) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    // Snapshot of the particle state in the scratch buffer (4 + 3 floats per particle <= 9).
+    float* snap = c->scratch;
+    CK(cudaMemcpyAsync(snap, c->pos, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(snap + 4 * c->np3, c->mom, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    const int step0 = c->step;
+    const bool fin0 = c->finalized, t0 = c->two_stage;
+    const int b0 = c->block;
+    const bool timing0 = c->timing;
+    c->timing = false;
+    c->finalized = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    bool best_ts = t0;
+    int best_b = b0;
+    const int blocks[3] = {128, 256, 512};
+    const int ksteps = c->prm.n_steps - 1 < step0 ? 0 : 1;
+    int r = COLAPM_OK;
+    for (int ts = 0; ts < 2 && r == COLAPM_OK; ++ts) {
+        for (int bi = 0; bi < 3 && r == COLAPM_OK; ++bi) {
+            c->two_stage = ts == 0;
+            c->block = blocks[bi];
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && r == COLAPM_OK; ++rep) {   // first repetition warms up
+                if (cudaMemcpyAsync(c->pos, snap, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(c->mom, snap + 4 * c->np3, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                    c->stream) != cudaSuccess) {
+                    r = COLAPM_E_CUDA;
+                    break;
+                }
+                c->step = ksteps ? step0 : 0;
+                cudaEventRecord(e0, c->stream);
+                r = compute_force(c);
+                if (r == COLAPM_OK && cudaGetLastError() == cudaSuccess) {
+                    const int i = c->step < c->prm.n_steps ? c->step : c->prm.n_steps - 1;
+                    if (launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, coef_for(c, i), 1,
+                                                 c->stream, c->block) != cudaSuccess)
+                        r = COLAPM_E_CUDA;
+                }
+                cudaEventRecord(e1, c->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) r = COLAPM_E_CUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (r == COLAPM_OK && ms < best) {
+                best = ms;
+                best_ts = c->two_stage;
+                best_b = c->block;
+            }
+        }
+    }
+    cudaMemcpyAsync(c->pos, snap, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->mom, snap + 4 * c->np3, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->step = step0;
+    c->finalized = fin0;
+    c->timing = timing0;
+    if (r != COLAPM_OK) {
+        c->two_stage = t0;
+        c->block = b0;
+        return r;
+    }
+    c->two_stage = best_ts;
+    c->block = best_b;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[{c->np, c->nm}] = {best_ts, best_b};
+    }
+    if (choice) {
+        choice[0] = best_ts ? 1 : 0;
+        choice[1] = best_b;
+    }
+    return COLAPM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batched mocks.
+
+struct colapm_batch {
+    int n = 0;
+    int nstreams = 0;                       // 0: not chosen yet
+    cudaStream_t caller = nullptr;          // the caller's stream (may be the legacy default stream)
+    cudaStream_t user = nullptr;            // internal stream the graph is captured on and launched from
+    std::vector<colapm_ctx*> ctx;
+    std::vector<cudaStream_t> ws;           // kMaxStreams worker streams
+    std::vector<cudaEvent_t> ev;            // fork + one join per worker
+    unsigned long long* seeds_h = nullptr;  // pinned [n]
+    unsigned long long* seeds_d = nullptr;  // [n]
+    double* acc_h = nullptr;                // pinned [n][3 nbins]
+    int nbins = 0;
+    double kmin = 0.0, kmax = 0.0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int kMaxStreams = 8;
+
+void batch_free(colapm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (colapm_ctx* c : b->ctx)
+        if (c) colapm_destroy(c);
+    for (cudaStream_t s : b->ws) cudaStreamDestroy(s);
+    if (b->user) cudaStreamDestroy(b->user);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->seeds_h) cudaFreeHost(b->seeds_h);
+    if (b->seeds_d) cudaFree(b->seeds_d);
+    if (b->acc_h) cudaFreeHost(b->acc_h);
+}
+
+// Enqueue the whole batch on b->user (captured or eager): seeds, fork, per-mock ICs + steps +
+// P(k) on worker stream i mod K, copies of the accumulators to the pinned buffer, join.
+int batch_enqueue(colapm_batch* b, int K) {
+    CK(cudaMemcpyAsync(b->seeds_d, b->seeds_h, b->n * sizeof(unsigned long long), cudaMemcpyHostToDevice, b->user));
+    CK(cudaEventRecord(b->ev[0], b->user));
+    for (int w = 0; w < K; ++w) CK(cudaStreamWaitEvent(b->ws[w], b->ev[0], 0));
+    for (int i = 0; i < b->n; ++i) {
+        colapm_ctx* c = b->ctx[i];
+        c->stream = b->ws[i % K];
+        int r = colapm_make_ics(c);
+        if (!r) r = colapm_step(c, -1);
+        if (!r) r = power_enqueue(c, b->nbins);
+        if (r) return r;
+        CK(cudaMemcpyAsync(b->acc_h + (size_t)i * 3 * b->nbins, c->pw_acc, 3 * b->nbins * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+    }
+    for (int w = 0; w < K; ++w) {
+        CK(cudaEventRecord(b->ev[1 + w], b->ws[w]));
+        CK(cudaStreamWaitEvent(b->user, b->ev[1 + w], 0));
+    }
+    return COLAPM_OK;
+}
+
+int batch_capture(colapm_batch* b, int K) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    CK(cudaStreamBeginCapture(b->user, cudaStreamCaptureModeRelaxed));
+    int r = batch_enqueue(b, K);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->user, &g);
+    if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) return COLAPM_E_CUDA;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? COLAPM_OK : COLAPM_E_CUDA;
+}
+
+float batch_time(colapm_batch* b) {   // one replay, ms
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, b->user);
+    cudaGraphLaunch(b->exec, b->user);
+    cudaEventRecord(e1, b->user);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+int colapm_batch_create(int n, const colapm_params* ps, int nstreams, void* stream, colapm_batch** out) {
+    if (!out || n < 1 || !ps || nstreams > kMaxStreams) return COLAPM_E_ARG;
+    *out = nullptr;
+    colapm_batch* b = new (std::nothrow) colapm_batch();
+    if (!b) return COLAPM_E_NOMEM;
+    b->n = n;
+    b->nstreams = nstreams > 0 ? nstreams : 0;
+    b->caller = static_cast<cudaStream_t>(stream);
+    b->ctx.assign(n, nullptr);
+    int r = COLAPM_OK;
+    if (cudaStreamCreateWithFlags(&b->user, cudaStreamNonBlocking) != cudaSuccess) r = COLAPM_E_CUDA;
+    for (int w = 0; w < kMaxStreams && !r; ++w) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) r = COLAPM_E_CUDA;
+        else b->ws.push_back(s);
+    }
+    for (int w = 0; w < kMaxStreams + 1 && !r; ++w) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) r = COLAPM_E_CUDA;
+        else b->ev.push_back(e);
+    }
+    if (!r && (cudaMallocHost(&b->seeds_h, n * sizeof(unsigned long long)) != cudaSuccess ||
+               cudaMalloc(&b->seeds_d, n * sizeof(unsigned long long)) != cudaSuccess))
+        r = COLAPM_E_NOMEM;
+    for (int i = 0; i < n && !r; ++i) {
+        r = colapm_create(&ps[i], b->ws[0], &b->ctx[i]);
+        if (!r) {
+            b->ctx[i]->seed_src = b->seeds_d + i;
+            b->seeds_h[i] = ps[i].seed;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tuned.find({ps[i].np, ps[i].nm});
+            if (it != g_tuned.end()) {
+                b->ctx[i]->two_stage = it->second.first;
+                b->ctx[i]->block = it->second.second;
+            }
+        }
+    }
+    if (r) {
+        cudaGetLastError();
+        batch_free(b);
+        delete b;
+        return r;
+    }
+    *out = b;
+    return COLAPM_OK;
+}
+
+int colapm_batch_run(colapm_batch* b, const unsigned long long* seeds, int nbins, double kmin, double kmax,
+                     double* k_out, double* p_out, long long* nmodes_out) {
+    if (!b || !k_out || !p_out || !nmodes_out || nbins < 1 || nbins > 4096) return COLAPM_E_ARG;
+    CK(cudaStreamSynchronize(b->caller));   // work the caller issued before this call comes first
+    if (!b->exec || nbins != b->nbins || kmin != b->kmin || kmax != b->kmax) {
+        for (colapm_ctx* c : b->ctx) {
+            c->stream = b->ws[0];
+            int r = power_prepare(c, nbins, kmin, kmax);
+            if (r) return r;
+        }
+        if (b->acc_h) cudaFreeHost(b->acc_h);
+        b->acc_h = nullptr;
+        if (cudaMallocHost(&b->acc_h, (size_t)b->n * 3 * nbins * sizeof(double)) != cudaSuccess) return COLAPM_E_NOMEM;
+        b->nbins = nbins;
+        b->kmin = kmin;
+        b->kmax = kmax;
+        // One eager pass initialises every kernel's launch configuration before capture.
+        int r = batch_enqueue(b, 1);
+        if (r) return r;
+        CK(cudaStreamSynchronize(b->user));
+        if (b->nstreams == 0) {   // choose the number of worker streams by timing replays
+            float best = 1e30f;
+            int bestk = 1;
+            for (int k = 1; k <= kMaxStreams; k *= 2) {
+                r = batch_capture(b, k);
+                if (r) return r;
+                batch_time(b);
+                const float ms = batch_time(b);
+                if (ms < best) {
+                    best = ms;
+                    bestk = k;
+                }
+            }
+            b->nstreams = bestk;
+        }
+        r = batch_capture(b, b->nstreams);
+        if (r) return r;
+    }
+    for (int i = 0; i < b->n; ++i) b->seeds_h[i] = seeds ? seeds[i] : b->ctx[i]->prm.seed;
+    CK(cudaGraphLaunch(b->exec, b->user));
+    CK(cudaStreamSynchronize(b->user));
+    for (int i = 0; i < b->n; ++i) {
+        colapm_ctx* c = b->ctx[i];
+        int r = pending_error(c);
+        if (r) return r;
+        power_finish(b->acc_h + (size_t)i * 3 * nbins, nbins, k_out + (size_t)i * nbins, p_out + (size_t)i * nbins,
+                     nmodes_out + (size_t)i * nbins);
+    }
+    return COLAPM_OK;
+}
+
+int colapm_batch_streams(const colapm_batch* b) { return b ? b->nstreams : COLAPM_E_ARG; }
+
+void colapm_batch_destroy(colapm_batch* b) {
+    if (!b) return;
+    if (b->user) cudaStreamSynchronize(b->user);
+    for (cudaStream_t s : b->ws) cudaStreamSynchronize(s);
+    batch_free(b);
+    delete b;
 }
 
 }  // extern "C"

@@ -61,24 +61,28 @@ __device__ __forceinline__ int power_bin(int n2, const int* lo, int nbins) {
 // Forward x pass (r2c) of N^2 rows of N reals into N^2 rows of N/2 complex (Nyquist dropped).
 // in_i64: int64 fixed-point density converted to delta = rho * scale - 1 (flags err[0] bit 0
 // when a cell has its top bit set); in_f32: real field.
+// `two_stage` selects the two-stage register FFT where it exists (256, 512, 1024 lines); the
+// shared-memory Stockham kernels otherwise.
 cudaError_t launch_fx_fwd_i64(int n_mesh, const unsigned long long* in, float2* out, const float2* tw,
-                              float scale, int* err, cudaStream_t s);
-cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const float2* tw, cudaStream_t s);
+                              float scale, int* err, cudaStream_t s, bool two_stage = true);
+cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const float2* tw, cudaStream_t s,
+                              bool two_stage = true);
 // Inverse x pass (c2r), in place, for `nfields` arrays spaced `field_stride` complex apart.
 cudaError_t launch_fx_inv(int n_mesh, float2* data, size_t field_stride, int nfields, const float2* tw,
-                          cudaStream_t s);
+                          cudaStream_t s, bool two_stage = true);
 // y pass in place (sign -1 forward, +1 inverse) on `nfields` arrays.
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
-                      cudaStream_t s);
+                      cudaStream_t s, bool two_stage = true);
 // z pass with the spectral multiply fused.
 cudaError_t launch_fz(int n_mesh, int mode, float2* in, ZOut out, const float2* tw, const float* sinc2,
-                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s);
+                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage = true);
 
 // --- launchers (pm_kernels.cu) --------------------------------------------------------------
-cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s);
+cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s,
+                           int block = 256);
 cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1, const float* psi2,
                                      const float* force, size_t np3, int nm, StepCoef c, int drift,
-                                     cudaStream_t s);
+                                     cudaStream_t s, int block = 256);
 cudaError_t launch_init_particles(float4* pos, float* mom, float* psi1, float* psi2, int np, int nm,
                                   float to_mesh, float d1, float d2, float p1, float p2, int cola,
                                   cudaStream_t s);
@@ -93,8 +97,10 @@ cudaError_t launch_import_state(float4* pos, float* mom, size_t np3, int nm, con
 cudaError_t launch_scale(float* dst, const float* src, size_t n, float f, cudaStream_t s);
 
 // --- launchers (ics_kernels.cu) -----------------------------------------------------------
-cudaError_t launch_gaussian_field(int np, unsigned long long seed, const float* amp_of_n2, float2* dk,
+// The seed is read from device memory, so a captured graph can be replayed with new seeds.
+cudaError_t launch_gaussian_field(int np, const unsigned long long* seed, const float* amp_of_n2, float2* dk,
                                   cudaStream_t s);
 cudaError_t launch_lpt2_source(const float* phi, size_t np3, float* src, cudaStream_t s);
+cudaError_t launch_set_u64(unsigned long long* dst, unsigned long long value, cudaStream_t s);
 
 }  // namespace colapm

@@ -5,9 +5,10 @@
 namespace colapm {
 
 template <int N, bool I64>
-static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float scale, int* err, cudaStream_t s) {
+static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float scale, int* err, cudaStream_t s,
+                            bool two_stage) {
     constexpr int n = N / 2;
-    if constexpr (F2Has<n>::value) {
+    if constexpr (F2Has<n>::value) if (two_stage) {
         using X = X2<n>;
         static int grid2 = 0;
         if (!grid2) {
@@ -32,9 +33,10 @@ static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float
 }
 
 template <int N>
-static cudaError_t fx_inv_t(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
+static cudaError_t fx_inv_t(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s,
+                            bool two_stage) {
     constexpr int n = N / 2;
-    if constexpr (F2Has<n>::value) {
+    if constexpr (F2Has<n>::value) if (two_stage) {
         using X = X2<n>;
         static int grid2 = 0;
         if (!grid2) {
@@ -59,18 +61,19 @@ static cudaError_t fx_inv_t(float2* data, size_t fstride, int nfields, const flo
 }
 
 cudaError_t launch_fx_fwd_i64(int n_mesh, const unsigned long long* in, float2* out, const float2* tw,
-                              float scale, int* err, cudaStream_t s) {
+                              float scale, int* err, cudaStream_t s, bool two_stage) {
     switch (n_mesh) {
-#define X(N) case N: return fx_fwd_t<N, true>(in, out, tw, scale, err, s);
+#define X(N) case N: return fx_fwd_t<N, true>(in, out, tw, scale, err, s, two_stage);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const float2* tw, cudaStream_t s) {
+cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const float2* tw, cudaStream_t s,
+                              bool two_stage) {
     switch (n_mesh) {
-#define X(N) case N: return fx_fwd_t<N, false>(in, out, tw, 0.0f, nullptr, s);
+#define X(N) case N: return fx_fwd_t<N, false>(in, out, tw, 0.0f, nullptr, s, two_stage);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -78,9 +81,9 @@ cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const fl
 }
 
 cudaError_t launch_fx_inv(int n_mesh, float2* data, size_t field_stride, int nfields, const float2* tw,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool two_stage) {
     switch (n_mesh) {
-#define X(N) case N: return fx_inv_t<N>(data, field_stride, nfields, tw, s);
+#define X(N) case N: return fx_inv_t<N>(data, field_stride, nfields, tw, s, two_stage);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;

@@ -5,8 +5,9 @@
 namespace colapm {
 
 template <int N, int S>
-static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
-    if constexpr (F2Has<N>::value) {
+static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s,
+                           bool two_stage) {
+    if constexpr (F2Has<N>::value) if (two_stage) {
         using K = K2<N>;
         constexpr size_t smem = sizeof(float2) * Xch<N, K::RA>::SIZE + sizeof(Tw2);
         static int grid2 = 0;
@@ -33,14 +34,16 @@ static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const floa
 }
 
 template <int N>
-static cudaError_t fy_t(int sign, float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
-    return sign < 0 ? fy_sign<N, -1>(data, fstride, nfields, tw, s) : fy_sign<N, +1>(data, fstride, nfields, tw, s);
+static cudaError_t fy_t(int sign, float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s,
+                        bool two_stage) {
+    return sign < 0 ? fy_sign<N, -1>(data, fstride, nfields, tw, s, two_stage)
+                    : fy_sign<N, +1>(data, fstride, nfields, tw, s, two_stage);
 }
 
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool two_stage) {
     switch (n_mesh) {
-#define X(N) case N: return fy_t<N>(sign, data, field_stride, nfields, tw, s);
+#define X(N) case N: return fy_t<N>(sign, data, field_stride, nfields, tw, s, two_stage);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;

@@ -6,8 +6,8 @@ namespace colapm {
 
 template <int N, int MODE>
 static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm,
-                           PowerArgs pw, cudaStream_t s) {
-    if constexpr (F2Has<N>::value) {
+                           PowerArgs pw, cudaStream_t s, bool two_stage) {
+    if constexpr (F2Has<N>::value) if (two_stage) {
         using Z = Z2<N, MODE>;
         const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
         static size_t configured2 = 0;
@@ -39,22 +39,22 @@ static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* 
 
 template <int N>
 static cudaError_t fz_t(int mode, float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv,
-                        float gnorm, const PowerArgs* pwp, cudaStream_t s) {
+                        float gnorm, const PowerArgs* pwp, cudaStream_t s, bool ts) {
     PowerArgs pw{};
     if (pwp) pw = *pwp;
     switch (mode) {
-        case Z_FORCE: return fz_mode<N, Z_FORCE>(in, out, tw, sinc2, deconv, gnorm, pw, s);
-        case Z_LPT1: return fz_mode<N, Z_LPT1>(in, out, tw, sinc2, deconv, gnorm, pw, s);
-        case Z_LPT2: return fz_mode<N, Z_LPT2>(in, out, tw, sinc2, deconv, gnorm, pw, s);
-        case Z_POWER: return fz_mode<N, Z_POWER>(in, out, tw, sinc2, deconv, gnorm, pw, s);
+        case Z_FORCE: return fz_mode<N, Z_FORCE>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
+        case Z_LPT1: return fz_mode<N, Z_LPT1>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
+        case Z_LPT2: return fz_mode<N, Z_LPT2>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
+        case Z_POWER: return fz_mode<N, Z_POWER>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_fz(int n_mesh, int mode, float2* in, ZOut out, const float2* tw, const float* sinc2,
-                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s) {
+                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage) {
     switch (n_mesh) {
-#define X(N) case N: return fz_t<N>(mode, in, out, tw, sinc2, deconv, gnorm, pw, s);
+#define X(N) case N: return fz_t<N>(mode, in, out, tw, sinc2, deconv, gnorm, pw, s, two_stage);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;

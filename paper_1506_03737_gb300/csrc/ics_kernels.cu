@@ -37,8 +37,9 @@ __device__ __forceinline__ float2 draw(unsigned long long m, unsigned long long 
 }
 
 // One thread per half-grid mode (iz, iy, ix < N/2): delta_k = amp(|n|^2) g, Hermitian on ix = 0.
-__global__ void k_gaussian_field(int n, unsigned long long seed, const float* __restrict__ amp_of_n2,
+__global__ void k_gaussian_field(int n, const unsigned long long* __restrict__ seedp, const float* __restrict__ amp_of_n2,
                                  float2* __restrict__ dk) {
+    const unsigned long long seed = *seedp;
     const int h = n / 2;
     const size_t total = (size_t)n * n * h;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,9 +78,17 @@ __global__ void k_lpt2_source(const float* __restrict__ phi, size_t n3, float* _
     src[i] = xx * yy + xx * zz + yy * zz - xy * xy - xz * xz - yz * yz;
 }
 
+__global__ void k_set_u64(unsigned long long* dst, unsigned long long value) { *dst = value; }
+
 }  // namespace
 
-cudaError_t launch_gaussian_field(int np, unsigned long long seed, const float* amp_of_n2, float2* dk, cudaStream_t s) {
+cudaError_t launch_set_u64(unsigned long long* dst, unsigned long long value, cudaStream_t s) {
+    k_set_u64<<<1, 1, 0, s>>>(dst, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian_field(int np, const unsigned long long* seed, const float* amp_of_n2, float2* dk,
+                                  cudaStream_t s) {
     const size_t total = (size_t)np * np * (np / 2);
     k_gaussian_field<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(np, seed, amp_of_n2, dk);
     return cudaGetLastError();

@@ -234,14 +234,14 @@ inline unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s) {
-    k_deposit<<<blocks(np3, 256), 256, 0, s>>>(pos, np3, nm, rho);
+cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s, int block) {
+    k_deposit<<<blocks(np3, block), block, 0, s>>>(pos, np3, nm, rho);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1, const float* psi2, const float* force,
-                                     size_t np3, int nm, StepCoef c, int drift, cudaStream_t s) {
-    k_gather_kick_drift<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift);
+                                     size_t np3, int nm, StepCoef c, int drift, cudaStream_t s, int block) {
+    k_gather_kick_drift<<<blocks(np3, block), block, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift);
     return cudaGetLastError();
 }
 
