@@ -133,6 +133,15 @@ int colapm_get_state(colapm_ctx* ctx, int* cell, float* offset, float* mom_cells
  * this call, which synchronises). Host or device. */
 int colapm_set_state(colapm_ctx* ctx, const int* cell, const float* offset, const float* mom_cells);
 
+/* Displacement Psi = x - q of every particle (xyz-interleaved [Np^3][3], Mpc/h, host or device),
+ * with the minimum-image convention and q the particle's site on the Lagrangian lattice (spacing
+ * L/Np, offset by half a PM cell). colapm_get_displacement writes it; colapm_set_displacement
+ * moves every particle to x = q + Psi (wrapped into the box) and leaves momenta and the step
+ * count alone, so that e.g. colapm_power measures a corrected field. |Psi| must stay below L;
+ * otherwise COLAPM_E_ARG (reported by this call, which synchronises). */
+int colapm_get_displacement(colapm_ctx* ctx, float* psi);
+int colapm_set_displacement(colapm_ctx* ctx, const float* psi);
+
 /* Deposit the current particles and copy the int64 fixed-point density (Nm^3, weight of one
  * particle = 2^45) to `mesh` (host or device). Synchronises. */
 int colapm_get_density(colapm_ctx* ctx, long long* mesh);

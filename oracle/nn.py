@@ -37,20 +37,28 @@ def conv(a, w, b):
     return out + b
 
 
-def forward(x, params):
-    """params: list of (W, b). Returns the output and the list of layer inputs/outputs."""
+def forward(x, params, store=None):
+    """params: list of (W, b). Returns the output and the list of layer inputs/outputs.
+
+    store (optional) maps each hidden activation to the values kept between layers, e.g.
+    bf16_round to model activations stored in BF16; arithmetic stays FP64."""
     acts = [x]
     h = x
     for l, (w, b) in enumerate(params):
         z = conv(h, w, b)
-        h = np.maximum(z, 0.0) if l < len(params) - 1 else z
+        if l < len(params) - 1:
+            h = np.maximum(z, 0.0)
+            if store is not None:
+                h = store(h)
+        else:
+            h = z
         acts.append(h)
     return h, acts
 
 
-def loss_and_grads(x, target, params):
+def loss_and_grads(x, target, params, store=None):
     """Mean squared error over all voxels and channels, and its gradients [(dW, db)] per layer."""
-    pred, acts = forward(x, params)
+    pred, acts = forward(x, params, store)
     diff = pred - target
     loss = float(np.mean(diff * diff))
     dz = 2.0 * diff / diff.size
@@ -70,6 +78,34 @@ def loss_and_grads(x, target, params):
                 da += shift(dz, (-d[0], -d[1], -d[2])) @ w[t]
             dz = da * (acts[l] > 0)
     return loss, grads
+
+
+def adam_step(params, grads, m1, m2, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) of flat arrays; t counts from 1.
+    Returns the new (params, m1, m2)."""
+    m1 = beta1 * m1 + (1.0 - beta1) * grads
+    m2 = beta2 * m2 + (1.0 - beta2) * grads * grads
+    mh = m1 / (1.0 - beta1 ** t)
+    vh = m2 / (1.0 - beta2 ** t)
+    return params - lr * mh / (np.sqrt(vh) + eps), m1, m2
+
+
+def flatten(params):
+    """Flat parameter vector: per layer W[27][c_out][c_in] then b[c_out]."""
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params])
+
+
+def unflatten(flat, sizes=(3, 16, 16, 16, 3)):
+    out, k = [], 0
+    for i in range(len(sizes) - 1):
+        nw = 27 * sizes[i + 1] * sizes[i]
+        w = np.asarray(flat[k:k + nw], dtype=np.float64).reshape(27, sizes[i + 1], sizes[i])
+        k += nw
+        b = np.asarray(flat[k:k + sizes[i + 1]], dtype=np.float64)
+        k += sizes[i + 1]
+        out.append((w, b))
+    assert k == len(flat)
+    return out
 
 
 def init_params(channels, seed=0, c_in=3, c_out=3, hidden=16):

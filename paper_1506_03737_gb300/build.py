@@ -17,7 +17,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcolapm.so")
 
 SOURCES = ["colapm.cu", "fft_x.cu", "fft_y.cu", "fft_z.cu", "pm_kernels.cu", "ics_kernels.cu",
-           "cosmology.cpp", "noalloc.cu"]
+           "cosmology.cpp", "noalloc.cu", "nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 
@@ -30,7 +30,8 @@ def _nvcc():
 
 def _headers():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    hs.append(os.path.join(ROOT, "include", "colapm.h"))
+    inc = os.path.join(ROOT, "include")
+    hs += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     return hs
 
 

@@ -33,6 +33,15 @@ class Params(ctypes.Structure):
                 ("cola", ctypes.c_int), ("deconv", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
+class NNConfig(ctypes.Structure):
+    _fields_ = [("s_in", ctypes.c_float), ("s_out", ctypes.c_float), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_ulonglong)]
+
+
+NN_PARAMS = 16467
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libcolapm.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
@@ -69,6 +78,19 @@ def _load():
         "colapm_batch_run": (I, [P, P, I, D, D, P, P, P]),
         "colapm_batch_streams": (I, [P]),
         "colapm_batch_destroy": (None, [P]),
+        "colapm_get_displacement": (I, [P, P]),
+        "colapm_set_displacement": (I, [P, P]),
+        "colapm_nn_default_config": (None, [ctypes.POINTER(NNConfig)]),
+        "colapm_nn_create": (I, [I, ctypes.POINTER(NNConfig), P, ctypes.POINTER(P)]),
+        "colapm_nn_destroy": (I, [P]),
+        "colapm_nn_set_params": (I, [P, P]),
+        "colapm_nn_get_params": (I, [P, P]),
+        "colapm_nn_forward": (I, [P, P, P, I]),
+        "colapm_nn_grads": (I, [P, P, P, P, ctypes.POINTER(D)]),
+        "colapm_nn_train_step": (I, [P, P, P, ctypes.POINTER(D)]),
+        "colapm_nn_steps": (I, [P]),
+        "colapm_nn_launches": (ctypes.c_longlong, [P]),
+        "colapm_nn_sync": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -264,3 +286,75 @@ def colapm_get_timing(ctx):
     cnt = np.zeros(len(PHASES), dtype=np.int64)
     _check(LIB.colapm_get_timing(ctx, _ptr(ms), _ptr(cnt)), "colapm_get_timing")
     return dict(zip(PHASES, ms)), dict(zip(PHASES, cnt))
+
+
+def colapm_get_displacement(ctx, psi):
+    _check(LIB.colapm_get_displacement(ctx, _ptr(psi)), "colapm_get_displacement")
+    return psi
+
+
+def colapm_set_displacement(ctx, psi):
+    _check(LIB.colapm_set_displacement(ctx, _ptr(psi)), "colapm_set_displacement")
+
+
+def nn_default_config(**kw):
+    c = NNConfig()
+    LIB.colapm_nn_default_config(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def colapm_nn_create(n, cfg=None, stream=0):
+    cfg = nn_default_config() if cfg is None else cfg
+    h = ctypes.c_void_p()
+    _check(LIB.colapm_nn_create(n, ctypes.byref(cfg), stream, ctypes.byref(h)), "colapm_nn_create")
+    return h
+
+
+def colapm_nn_destroy(nn):
+    _check(LIB.colapm_nn_destroy(nn), "colapm_nn_destroy")
+
+
+def colapm_nn_set_params(nn, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != NN_PARAMS:
+        raise ValueError(f"expected {NN_PARAMS} parameters")
+    _check(LIB.colapm_nn_set_params(nn, _ptr(a)), "colapm_nn_set_params")
+
+
+def colapm_nn_get_params(nn):
+    out = np.empty(NN_PARAMS, np.float32)
+    _check(LIB.colapm_nn_get_params(nn, _ptr(out)), "colapm_nn_get_params")
+    return out
+
+
+def colapm_nn_forward(nn, psi, out, add=False):
+    _check(LIB.colapm_nn_forward(nn, _ptr(psi), _ptr(out), int(add)), "colapm_nn_forward")
+    return out
+
+
+def colapm_nn_grads(nn, psi, target):
+    g = np.empty(NN_PARAMS, np.float32)
+    loss = ctypes.c_double()
+    _check(LIB.colapm_nn_grads(nn, _ptr(psi), _ptr(target), _ptr(g), ctypes.byref(loss)), "colapm_nn_grads")
+    return g, loss.value
+
+
+def colapm_nn_train_step(nn, psi, target, want_loss=True):
+    loss = ctypes.c_double()
+    _check(LIB.colapm_nn_train_step(nn, _ptr(psi), _ptr(target), ctypes.byref(loss) if want_loss else None),
+           "colapm_nn_train_step")
+    return loss.value if want_loss else None
+
+
+def colapm_nn_steps(nn):
+    return LIB.colapm_nn_steps(nn)
+
+
+def colapm_nn_launches(nn):
+    return LIB.colapm_nn_launches(nn)
+
+
+def colapm_nn_sync(nn):
+    _check(LIB.colapm_nn_sync(nn), "colapm_nn_sync")

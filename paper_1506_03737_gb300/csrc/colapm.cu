@@ -563,6 +563,27 @@ int colapm_set_state(colapm_ctx* c, const int* cell, const float* off, const flo
     return pending_error(c);
 }
 
+int colapm_get_displacement(colapm_ctx* c, float* psi) {
+    if (!c || !psi) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    float* d = is_device_ptr(psi) ? psi : c->scratch;
+    CKL(launch_export_displacement(c->pos, c->np, c->nm, (float)(c->prm.box / c->nm), d, c->stream));
+    if (d != psi) copy_out(c, psi, d, 3 * c->np3 * sizeof(float));
+    return pending_error(c);
+}
+
+int colapm_set_displacement(colapm_ctx* c, const float* psi) {
+    if (!c || !psi) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    const float* d = psi;
+    if (!is_device_ptr(psi)) {
+        CK(cudaMemcpyAsync(c->scratch, psi, 3 * c->np3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        d = c->scratch;
+    }
+    CKL(launch_import_displacement(c->pos, c->np, c->nm, (float)(c->nm / c->prm.box), d, c->err, c->stream));
+    return pending_error(c);
+}
+
 int colapm_get_density(colapm_ctx* c, long long* mesh) {
     if (!c || !mesh) return COLAPM_E_ARG;
     if (!c->has_ics) return COLAPM_E_STATE;

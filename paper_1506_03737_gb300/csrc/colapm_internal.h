@@ -94,6 +94,9 @@ cudaError_t launch_export_state(const float4* pos, const float* mom, size_t np3,
                                 float* off_xyz, float* mom_xyz, cudaStream_t s);
 cudaError_t launch_import_state(float4* pos, float* mom, size_t np3, int nm, const int* cell_xyz,
                                 const float* off_xyz, const float* mom_xyz, int* err, cudaStream_t s);
+cudaError_t launch_export_displacement(const float4* pos, int np, int nm, float cell, float* psi, cudaStream_t s);
+cudaError_t launch_import_displacement(float4* pos, int np, int nm, float to_mesh, const float* psi, int* err,
+                                       cudaStream_t s);
 cudaError_t launch_scale(float* dst, const float* src, size_t n, float f, cudaStream_t s);
 
 // --- launchers (ics_kernels.cu) -----------------------------------------------------------

@@ -225,6 +225,58 @@ __global__ void k_import_state(float4* __restrict__ pos, float* __restrict__ mom
     }
 }
 
+// Psi = x - q in Mpc/h with the minimum-image convention, q = (site * Nm/Np + 1/2) cells.
+__global__ void k_export_displacement(const float4* __restrict__ pos, int np, int nm, float cell,
+                                      float* __restrict__ psi) {
+    const size_t np3 = (size_t)np * np * np;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const float4 P = pos[p];
+    const unsigned c = __float_as_uint(P.w), u = (unsigned)nm;
+    const int cc[3] = {(int)(c % u), (int)((c / u) % u), (int)(c / (u * u))};
+    const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
+    const float off[3] = {P.x, P.y, P.z};
+    const int ratio = nm / np, h = nm / 2;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        int di = cc[j] - site[j] * ratio;
+        di += di < -h ? nm : (di >= h ? -nm : 0);
+        float d = (float)di + (off[j] - 0.5f);
+        d += d < -(float)h ? (float)nm : (d >= (float)h ? -(float)nm : 0.0f);
+        psi[3 * p + j] = d * cell;
+    }
+}
+
+// x = q + Psi (Psi in Mpc/h, xyz-interleaved); momenta are left alone.
+__global__ void k_import_displacement(float4* __restrict__ pos, int np, int nm, float to_mesh,
+                                      const float* __restrict__ psi, int* err) {
+    const size_t np3 = (size_t)np * np * np;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
+    const int ratio = nm / np;
+    int cell[3];
+    float o[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float s = psi[3 * p + j] * to_mesh;
+        if (!(fabsf(s) < (float)nm)) {
+            atomicOr(err, 2);
+            return;
+        }
+        const float u = 0.5f + s;
+        float fl = floorf(u);
+        float r = u - fl;
+        if (r >= 1.0f) { r = 0.0f; fl += 1.0f; }
+        int cc = (site[j] * ratio + (int)fl) % nm;
+        if (cc < 0) cc += nm;
+        cell[j] = cc;
+        o[j] = r;
+    }
+    const unsigned lin = (unsigned)cell[0] + (unsigned)nm * ((unsigned)cell[1] + (unsigned)nm * (unsigned)cell[2]);
+    pos[p] = make_float4(o[0], o[1], o[2], __uint_as_float(lin));
+}
+
 __global__ void k_scale(float* __restrict__ dst, const float* __restrict__ src, size_t n, float f) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = src[i] * f;
@@ -273,6 +325,19 @@ cudaError_t launch_export_state(const float4* pos, const float* mom, size_t np3,
 cudaError_t launch_import_state(float4* pos, float* mom, size_t np3, int nm, const int* cell_xyz, const float* off_xyz,
                                 const float* mom_xyz, int* err, cudaStream_t s) {
     k_import_state<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, np3, nm, cell_xyz, off_xyz, mom_xyz, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_displacement(const float4* pos, int np, int nm, float cell, float* psi, cudaStream_t s) {
+    const size_t np3 = (size_t)np * np * np;
+    k_export_displacement<<<blocks(np3, 256), 256, 0, s>>>(pos, np, nm, cell, psi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_displacement(float4* pos, int np, int nm, float to_mesh, const float* psi, int* err,
+                                       cudaStream_t s) {
+    const size_t np3 = (size_t)np * np * np;
+    k_import_displacement<<<blocks(np3, 256), 256, 0, s>>>(pos, np, nm, to_mesh, psi, err);
     return cudaGetLastError();
 }
 

@@ -76,3 +76,34 @@ def test_bf16_round_half_to_even():
     vals = np.array([one, one + ulp / 2, one + 1.5 * ulp, one + ulp / 4, -3.0], dtype=np.float32)
     out = nn.bf16_round(vals)
     assert list(out) == [1.0, 1.0, one + 2 * ulp, 1.0, -3.0]
+
+
+def test_flatten_roundtrip_and_size():
+    params = nn.init_params(None, seed=5)
+    flat = nn.flatten(params)
+    assert flat.size == 16467                      # 27*(3*16 + 16*16*2 + 16*3) + 16*3 + 3
+    back = nn.unflatten(flat)
+    for (w, b), (w2, b2) in zip(params, back):
+        assert np.array_equal(w, w2) and np.array_equal(b, b2)
+
+
+def test_adam_closed_forms():
+    # Step 1: m_hat = g and v_hat = g^2, so each weight moves by -lr g/(|g| + eps), i.e. -lr sign(g).
+    g = np.array([3.0, -2e-3, 5e-1, 0.0])
+    p0 = np.zeros(4)
+    p1, m1, m2 = nn.adam_step(p0, g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    assert np.allclose(p1[:3], -0.01 * np.sign(g[:3]), rtol=1e-5) and p1[3] == 0.0
+    # A constant gradient keeps m_hat = g and v_hat = g^2 at every step: the same move each time.
+    p, a, b = p1, m1, m2
+    for t in range(2, 6):
+        p, a, b = nn.adam_step(p, g, a, b, t, lr=0.01)
+    assert np.allclose(p[:3], -0.05 * np.sign(g[:3]), rtol=1e-5)
+
+
+def test_stored_activation_rounding_changes_only_storage():
+    x, t, params = small_problem(seed=7)
+    out, acts = nn.forward(x, params, store=nn.bf16_round)
+    for a in acts[1:-1]:
+        assert np.array_equal(a, nn.bf16_round(a))
+    ref, _ = nn.forward(x, params)
+    assert np.sqrt(np.mean((out - ref) ** 2)) < 1e-2 * np.sqrt(np.mean(ref ** 2))
