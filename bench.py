@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -205,6 +206,72 @@ def run_batch(C, stream, rank, args):
         C.colapm_batch_destroy(b)
 
 
+# forward FLOPs per voxel of the 3-16-16-16-3 network with 3^3 taps (true channel counts)
+NN_FLOP_VOXEL = 2 * 27 * (3 * 16 + 16 * 16 + 16 * 16 + 16 * 3)
+
+
+def run_learned(C, stream, rank, train_steps=3000):
+    """The learned correction on 128^3 particles in 256 Mpc/h: coarse = 128^3 mesh, 5 steps; fine =
+    384^3 mesh, 50 steps; 256 seeds, 224 to train and 32 to test; one Adam step per pair draw."""
+    import torch
+    from paper_1506_03737_gb300 import learned
+    pc, pf = learned.pair_params(128, 256.0, 128, 5, 384, 50,
+                                 {x: workloads.COSMO[x] for x in ("omega_m", "h", "n_s", "sigma8")})
+    seeds = [100000 * rank + s for s in range(256)]
+    t0 = time.perf_counter()
+    pairs = learned.Pairs(pc, pf, seeds, nbins=24, stream=stream.cuda_stream)
+    gen = time.perf_counter() - t0
+    train_idx, test_idx = list(range(224)), list(range(224, 256))
+    s_in, s_out = pairs.scales(train_idx)
+    net = C.colapm_nn_create(128, C.nn_default_config(s_in=s_in, s_out=s_out, lr=1e-3, seed=1), stream.cuda_stream)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        learned.train(net, pairs, train_idx, train_steps, seed=rank)
+        train_s = time.perf_counter() - t0
+        res = learned.evaluate(net, pairs, test_idx, cross_seeds=4)
+        # forward (inference) time with CUDA events on the network's stream
+        out = torch.empty_like(pairs.coarse[0])
+        for _ in range(3):
+            C.colapm_nn_forward(net, pairs.coarse[0], out)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        ev0.record(stream)
+        for _ in range(reps):
+            C.colapm_nn_forward(net, pairs.coarse[0], out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = ev0.elapsed_time(ev1) / reps
+        tf = NN_FLOP_VOXEL * 128 ** 3 / (fwd_ms / 1e3) / 1e12
+        _, peak_src = peaks()
+        tpeak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"] \
+            if peak_src == "measured" else 1700.0
+        per_coarse = pairs.secs["coarse"] / len(seeds)
+        per_fine = pairs.secs["fine"] / len(seeds)
+        r_hi = lambda r: float(np.nanmean(r[len(r) // 2:]))          # noqa: E731
+        return {
+            "workload": "128^3 particles, L = 256 Mpc/h; coarse 128^3 mesh 5 COLA steps, fine 384^3 mesh "
+                        "50 steps, same seeds; net 3-16-16-16-3 periodic 3^3 convs, BF16 x BF16 -> FP32",
+            "pairs": len(seeds), "train_pairs": len(train_idx), "test_pairs": len(test_idx),
+            "pair_generation_s": gen, "train_steps": train_steps, "train_ms_per_step": 1e3 * train_s / train_steps,
+            "forward_ms": fwd_ms,
+            "pk_err_plain": res["pk_err_plain"], "pk_err_net": res["pk_err_net"],
+            "mse_plain_mpc2": res["mse_plain"], "mse_net_mpc2": res["mse_net"],
+            "r_high_k_plain": r_hi(res["r_plain"]), "r_high_k_net": r_hi(res["r_net"]),
+            "mocks_per_hour_coarse_plus_net": 3600.0 / (per_coarse + fwd_ms / 1e3),
+            "mocks_per_hour_fine": 3600.0 / per_fine,
+            "note": "pk_err = mean over 24 log k-bins below the particle Nyquist frequency of |<P>/<P_fine> - 1| "
+                    "on the 32 test seeds, all spectra on the 128^3 mesh; r_high_k = mean cross-correlation with "
+                    "the fine density over the upper 12 bins (4 test seeds)",
+            "conv_roofline": {"bound": "tensor", "kernel": "forward (4 conv launches + input pack)",
+                              "achieved": tf, "peak": tpeak, "unit": "TFLOP/s", "frac": tf / tpeak,
+                              "flop_per_voxel": NN_FLOP_VOXEL, "peak_source": f"{peak_src} bf16_tflops_sustained"},
+        }
+    finally:
+        C.colapm_nn_destroy(net)
+        pairs.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -335,6 +402,8 @@ def main():
     C.colapm_destroy(ctx)
     if not args.no_batch:
         line["batch"] = run_batch(C, stream, rank, args)
+    if not args.no_learned:
+        line["learned"] = run_learned(C, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
