@@ -40,7 +40,7 @@ enum {
     COLAPM_E_NOMEM = -2,    /* device or host allocation failed                                 */
     COLAPM_E_CUDA = -3,     /* a CUDA runtime call or kernel launch failed                      */
     COLAPM_E_OVERFLOW = -4, /* a density cell reached 2^63 in the int64 fixed-point deposit     */
-    COLAPM_E_TIMEOUT = -5,  /* a bounded device-side wait gave up                               */
+    COLAPM_E_TIMEOUT = -5,  /* a bounded device-side wait gave up (result of that call invalid)  */
     COLAPM_E_STATE = -6     /* call out of order (e.g. colapm_step before initial conditions)   */
 };
 
@@ -193,12 +193,20 @@ long long colapm_kernel_launches(const colapm_ctx* ctx);
 
 /* ---- autotuning ------------------------------------------------------------------------- */
 /* Time the candidate configurations of this context on its current state -- the FFT engine
- * (two-stage register FFT or shared-memory Stockham, where both exist) and the block size of
+ * (fused x-y passes through an L2-resident ring for N_m = 512 and 1024, the two-stage register
+ * FFT, or shared-memory Stockham, where each exists) and the block size of
  * the particle kernels (128, 256, 512) -- keep the fastest, and remember it for later contexts
  * with the same (np, nm) in this process. The particle state and step counter are restored.
- * Requires initial conditions (COLAPM_E_STATE). Synchronises. `choice` (may be NULL) receives
- * {two_stage (0/1), block}. */
+ * Requires initial conditions (COLAPM_E_STATE). Synchronises. `choice` (may be NULL, else 3 ints)
+ * receives {two_stage (0/1), block, fused x-y passes (0 or 3)}. */
 int colapm_autotune(colapm_ctx* ctx, int* choice);
+
+/* Select the configuration explicitly (e.g. to compare engines or to pin a choice): fused x-y
+ * passes as a bit mask (1 forward, 2 inverse, 3 both; default 0; ignored where N_m has none),
+ * two-stage register FFT (else Stockham) and the particle-kernel block size (128, 256 or 512);
+ * COLAPM_E_ARG otherwise. All engines compute the same transforms; fused and two-stage passes
+ * give bit-identical results. */
+int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
 
 /* ---- batched mocks (many independent realisations of uneven sizes) ----------------------- */
 typedef struct colapm_batch colapm_batch;   /* opaque; owns its contexts and graph */

@@ -27,7 +27,7 @@ import math
 
 import numpy as np
 
-from .fft import fftn, ifftn
+from .fft import fft_axis, fftn, ifftn
 from .ics import wavevectors, signed_index
 
 QBITS = 15
@@ -80,8 +80,11 @@ def cic_window(nm):
     return wx * wy * wz
 
 
-def force_mesh(delta, box, deconv=1):
-    """Three real meshes F_j = -d psi / d x_j (Mpc/h), lap psi = delta (§2.4 steps 2-3)."""
+def force_mesh(delta, box, deconv=1, fft=None):
+    """Three real meshes F_j = -d psi / d x_j (Mpc/h), lap psi = delta (§2.4 steps 2-3).
+
+    fft="numpy" takes numpy's FFT as the transform primitive (for meshes where the oracle's own
+    FFT, pinned against the DFT definition, is too slow); the operator is the same."""
     nm = delta.shape[0]
     kx, ky, kz, nyq = wavevectors(nm, box)
     k2 = kx * kx + ky * ky + kz * kz
@@ -89,8 +92,27 @@ def force_mesh(delta, box, deconv=1):
     ok = (k2 > 0) & ~nyq
     win = cic_window(nm) ** deconv
     mult[ok] = 1.0 / (k2[ok] * win[ok])
-    dk = fftn(delta)
-    return np.stack([ifftn(1j * kv * dk * mult).real for kv in (kx, ky, kz)])
+    fwd, inv = (np.fft.fftn, np.fft.ifftn) if fft == "numpy" else (fftn, ifftn)
+    dk = fwd(delta)
+    return np.stack([inv(1j * kv * dk * mult).real for kv in (kx, ky, kz)])
+
+
+def planar_force_1d(delta_1d, box, deconv=1):
+    """Force along the axis of a density that varies along one axis only (§2.4 steps 2-3 reduced
+    to one dimension: only modes with the other two indices zero are present, so k^2 = k_a^2 and
+    the CIC window is the single factor sinc^2(pi n_a / N); the Nyquist index is excluded)."""
+    nm = delta_1d.shape[0]
+    s = signed_index(nm).astype(np.float64)
+    k = s * 2.0 * math.pi / box
+    x = math.pi * s / nm
+    with np.errstate(divide="ignore", invalid="ignore"):
+        sinc = np.where(s == 0, 1.0, np.sin(x) / np.where(s == 0, 1.0, x))
+    win = (sinc * sinc) ** deconv
+    mult = np.zeros(nm)
+    ok = (s != 0) & (np.arange(nm) != nm // 2)
+    mult[ok] = 1.0 / (k[ok] * k[ok] * win[ok])
+    dk = fft_axis(np.asarray(delta_1d, dtype=np.complex128), 0, -1)
+    return (fft_axis(1j * k * dk * mult, 0, +1) / nm).real
 
 
 def cic_gather(force, u):

@@ -74,6 +74,7 @@ def _load():
         "colapm_strerror": (ctypes.c_char_p, [I]),
         "colapm_power_noalloc": (I, [P, P, ctypes.c_longlong, I, D, I, D, D, P, P, P, P]),
         "colapm_autotune": (I, [P, P]),
+        "colapm_set_engine": (I, [P, I, I, I]),
         "colapm_batch_create": (I, [I, P, I, P, ctypes.POINTER(P)]),
         "colapm_batch_run": (I, [P, P, I, D, D, P, P, P]),
         "colapm_batch_streams": (I, [P]),
@@ -247,9 +248,13 @@ def colapm_power_noalloc(cell, offset, n_particles, nm, box, nbins, kmin=0.0, km
 
 
 def colapm_autotune(ctx):
-    choice = np.zeros(2, dtype=np.int32)
+    choice = np.zeros(3, dtype=np.int32)
     _check(LIB.colapm_autotune(ctx, _ptr(choice)), "colapm_autotune")
-    return {"two_stage": bool(choice[0]), "block": int(choice[1])}
+    return {"two_stage": bool(choice[0]), "block": int(choice[1]), "fused": int(choice[2])}
+
+
+def colapm_set_engine(ctx, fused=3, two_stage=True, block=256):
+    _check(LIB.colapm_set_engine(ctx, int(fused), int(two_stage), int(block)), "colapm_set_engine")
 
 
 def colapm_batch_create(params_list, nstreams=0, stream=0):

@@ -31,7 +31,7 @@ struct colapm_ctx {
     float2* tw_p = nullptr;              // exp(-2 pi i t / np)
     float* sinc2_m = nullptr;            // sinc^2(pi n / nm) per FFT bin
     float* amp_p = nullptr;              // Gaussian-field amplitude per integer |n|^2 of the IC grid
-    int* err = nullptr;                  // device error bits: 1 overflow, 2 bad state import
+    int* err = nullptr;                  // device error bits: 1 overflow, 2 bad state import, 4 wait timeout
     // power-spectrum tables (grown on demand)
     int* pw_bin = nullptr;               // |n|^2 thresholds of the bins
     double* pw_acc = nullptr;            // ksum[nb], psum[nb], cnt[nb] (as u64)
@@ -39,6 +39,9 @@ struct colapm_ctx {
     unsigned long long* d_seed = nullptr;          // device seed of the Gaussian field
     const unsigned long long* seed_src = nullptr;  // the seed the ICs read (own, or a batch slot)
     bool two_stage = true;               // FFT engine for 256/512/1024 lines (autotuned)
+    int fused = 0;                       // fused x-y passes where supported: bit 0 forward, bit 1 inverse (autotuned)
+    float2* xy_ring = nullptr;           // L2-resident ring of intermediate planes of the fused passes
+    int* xy_ctr = nullptr;               // their work ticket and per-plane completion counters
     int block = 256;                     // particle-kernel block size (autotuned)
     int step = 0;
     long long launches = 0;              // kernels launched by this context
@@ -101,7 +104,7 @@ bool is_device_ptr(const void* p) {
 
 void free_all(colapm_ctx* c) {
     void* ptrs[] = {c->rho, c->F, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
-                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed};
+                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed, c->xy_ring, c->xy_ctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& v : c->ev)
@@ -127,6 +130,7 @@ int pending_error(colapm_ctx* c) {
     if (h) CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
     if (h & 1) return COLAPM_E_OVERFLOW;
     if (h & 2) return COLAPM_E_ARG;
+    if (h & 4) return COLAPM_E_TIMEOUT;
     return COLAPM_OK;
 }
 
@@ -143,6 +147,8 @@ int deposit(colapm_ctx* c) {
     return COLAPM_OK;
 }
 
+bool use_xy(const colapm_ctx* c, int bit) { return (c->fused & bit) && c->xy_ring != nullptr; }
+
 float density_scale(const colapm_ctx* c) {
     const double m = (double)c->nm / c->np;
     return (float)(m * m * m * std::ldexp(1.0, -45));
@@ -152,6 +158,10 @@ float density_scale(const colapm_ctx* c) {
 int density_xy(colapm_ctx* c) {
     Phase ph(c, COLAPM_PHASE_FFT_FWD);
     float2* d = reinterpret_cast<float2*>(c->F);
+    if (use_xy(c, 1)) {
+        CKL(launch_xy_fwd(c->nm, c->rho, d, c->tw_m, density_scale(c), c->xy_ring, c->xy_ctr, c->err, c->stream));
+        return COLAPM_OK;
+    }
     CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, c->two_stage));
     CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream, c->two_stage));
     return COLAPM_OK;
@@ -176,8 +186,12 @@ int compute_force(colapm_ctx* c) {
     }
     {
         Phase ph(c, COLAPM_PHASE_FFT_INV);
-        CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage));
-        CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage));
+        if (use_xy(c, 2)) {
+            CKL(launch_xy_inv(c->nm, d, fs, 3, c->tw_m, c->xy_ring, c->xy_ctr, c->err, c->stream));
+        } else {
+            CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage));
+            CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage));
+        }
     }
     return COLAPM_OK;
 }
@@ -281,6 +295,9 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
               dalloc(&c->tw_p, (size_t)c->np) == cudaSuccess && dalloc(&c->sinc2_m, (size_t)c->nm) == cudaSuccess &&
               dalloc(&c->amp_p, (size_t)3 * (c->np / 2) * (c->np / 2) + 1) == cudaSuccess &&
               dalloc(&c->err, 4) == cudaSuccess && dalloc(&c->d_seed, 1) == cudaSuccess;
+    if (ok && xy_supported(c->nm))
+        ok = dalloc(reinterpret_cast<char**>(&c->xy_ring), xy_ring_bytes(c->nm)) == cudaSuccess &&
+             dalloc(&c->xy_ctr, xy_ctr_ints(c->nm, 3)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -723,7 +740,19 @@ int colapm_get_timing(colapm_ctx* c, double* ms, long long* launches) {
 // Autotuning: FFT engine and particle-kernel block size, timed on the context's own state.
 
 static std::mutex g_tune_mu;
-static std::map<std::pair<int, int>, std::pair<bool, int>> g_tuned;   // (np, nm) -> (two_stage, block)
+struct Tuned {
+    bool two_stage;
+    int fused, block;
+};
+static std::map<std::pair<int, int>, Tuned> g_tuned;   // (np, nm) -> choice
+
+int colapm_set_engine(colapm_ctx* c, int fused, int two_stage, int block) {
+    if (!c || (block != 128 && block != 256 && block != 512) || fused < 0 || fused > 3) return COLAPM_E_ARG;
+    c->fused = fused;
+    c->two_stage = two_stage != 0;
+    c->block = block;
+    return COLAPM_OK;
+}
 
 int colapm_autotune(colapm_ctx* c, int* choice) {
     if (!c) return COLAPM_E_ARG;
@@ -734,6 +763,7 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     CK(cudaMemcpyAsync(snap + 4 * c->np3, c->mom, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     const int step0 = c->step;
     const bool fin0 = c->finalized, t0 = c->two_stage;
+    const int f0 = c->fused;
     const int b0 = c->block;
     const bool timing0 = c->timing;
     c->timing = false;
@@ -743,13 +773,16 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     bool best_ts = t0;
+    int best_f = f0;
     int best_b = b0;
     const int blocks[3] = {128, 256, 512};
     const int ksteps = c->prm.n_steps - 1 < step0 ? 0 : 1;
     int r = COLAPM_OK;
-    for (int ts = 0; ts < 2 && r == COLAPM_OK; ++ts) {
+    // engines: 0 fused x-y passes (where the mesh size has them), 1 two-stage, 2 Stockham
+    for (int eng = c->xy_ring ? 0 : 1; eng < 3 && r == COLAPM_OK; ++eng) {
         for (int bi = 0; bi < 3 && r == COLAPM_OK; ++bi) {
-            c->two_stage = ts == 0;
+            c->fused = eng == 0 ? 3 : 0;
+            c->two_stage = eng < 2;
             c->block = blocks[bi];
             float ms = 0.0f;
             for (int rep = 0; rep < 2 && r == COLAPM_OK; ++rep) {   // first repetition warms up
@@ -775,6 +808,7 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
             if (r == COLAPM_OK && ms < best) {
                 best = ms;
                 best_ts = c->two_stage;
+                best_f = c->fused;
                 best_b = c->block;
             }
         }
@@ -789,18 +823,21 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     c->timing = timing0;
     if (r != COLAPM_OK) {
         c->two_stage = t0;
+        c->fused = f0;
         c->block = b0;
         return r;
     }
     c->two_stage = best_ts;
+    c->fused = best_f;
     c->block = best_b;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[{c->np, c->nm}] = {best_ts, best_b};
+        g_tuned[{c->np, c->nm}] = Tuned{best_ts, best_f, best_b};
     }
     if (choice) {
         choice[0] = best_ts ? 1 : 0;
         choice[1] = best_b;
+        choice[2] = c->xy_ring ? best_f : 0;
     }
     return COLAPM_OK;
 }
@@ -935,8 +972,9 @@ int colapm_batch_create(int n, const colapm_params* ps, int nstreams, void* stre
             std::lock_guard<std::mutex> lock(g_tune_mu);
             auto it = g_tuned.find({ps[i].np, ps[i].nm});
             if (it != g_tuned.end()) {
-                b->ctx[i]->two_stage = it->second.first;
-                b->ctx[i]->block = it->second.second;
+                b->ctx[i]->two_stage = it->second.two_stage;
+                b->ctx[i]->fused = it->second.fused;
+                b->ctx[i]->block = it->second.block;
             }
         }
     }

@@ -74,6 +74,17 @@ cudaError_t launch_fx_inv(int n_mesh, float2* data, size_t field_stride, int nfi
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
                       cudaStream_t s, bool two_stage = true);
 // z pass with the spectral multiply fused.
+// Fused x-y passes (N = 512, 1024): forward r2c x + y of the int64 density into the half
+// spectrum `out`; inverse y + c2r x of `nfields` spectra in place. `ring` holds xy_ring_bytes(N)
+// and `ctr` xy_ctr_ints(N, nfields) ints (the launch zeroes them); err bit 4 = a bounded wait gave up.
+bool xy_supported(int nm);
+size_t xy_ring_bytes(int nm);
+size_t xy_ctr_ints(int nm, int nfields);
+cudaError_t launch_xy_fwd(int nm, const unsigned long long* rho, float2* out, const float2* tw, float scale,
+                          float2* ring, int* ctr, int* err, cudaStream_t s);
+cudaError_t launch_xy_inv(int nm, float2* data, size_t fstride, int nfields, const float2* tw, float2* ring, int* ctr,
+                          int* err, cudaStream_t s);
+
 cudaError_t launch_fz(int n_mesh, int mode, float2* in, ZOut out, const float2* tw, const float* sinc2,
                       int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage = true);
 

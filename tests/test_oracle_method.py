@@ -260,3 +260,21 @@ def test_power_single_mode_and_cross_correlation():
     assert abs(r[b[0]] - 1) < 1e-12
     r = power.cross_correlation(dk, -dk, BOX, 20, kf, kf * n / 2)
     assert abs(r[b[0]] + 1) < 1e-12
+
+
+def test_planar_force_reduces_the_3d_operator_to_one_axis():
+    # A density that varies along x only has modes with n_y = n_z = 0: the 3-D force mesh is the
+    # 1-D solution along x, constant in y and z, and the other two components vanish.
+    from oracle import pm as opm
+    nm, box = 16, 40.0
+    rng = np.random.default_rng(3)
+    d1 = rng.standard_normal(nm)
+    delta = np.broadcast_to(d1[None, None, :], (nm, nm, nm)).copy()
+    for deconv in (0, 1, 2):
+        f3 = opm.force_mesh(delta, box, deconv)
+        f1 = opm.planar_force_1d(d1, box, deconv)
+        assert np.allclose(f3[0], f1[None, None, :], atol=1e-12)
+        assert np.abs(f3[1]).max() < 1e-12 and np.abs(f3[2]).max() < 1e-12
+    # numpy's FFT as the primitive gives the same operator
+    delta = rng.standard_normal((nm, nm, nm))
+    assert np.allclose(opm.force_mesh(delta, box, 1, fft="numpy"), opm.force_mesh(delta, box, 1), atol=1e-10)
