@@ -40,6 +40,7 @@ struct colapm_ctx {
     const unsigned long long* seed_src = nullptr;  // the seed the ICs read (own, or a batch slot)
     bool two_stage = true;               // FFT engine for 256/512/1024 lines (autotuned)
     int fused = 0;                       // fused x-y passes where supported: bit 0 forward, bit 1 inverse (autotuned)
+    bool rho_clean = false;              // rho is all zero (the forward x pass clears it as it reads)
     float2* xy_ring = nullptr;           // L2-resident ring of intermediate planes of the fused passes
     int* xy_ctr = nullptr;               // their work ticket and per-plane completion counters
     int block = 256;                     // particle-kernel block size (autotuned)
@@ -142,7 +143,8 @@ int copy_out(colapm_ctx* c, void* dst, const void* src, size_t bytes) {
 
 int deposit(colapm_ctx* c) {
     Phase ph(c, COLAPM_PHASE_DEPOSIT);
-    CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
+    if (!c->rho_clean) CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
+    c->rho_clean = false;
     CKL(launch_deposit(c->pos, c->np3, c->nm, c->rho, c->stream, c->block));
     return COLAPM_OK;
 }
@@ -158,11 +160,14 @@ float density_scale(const colapm_ctx* c) {
 int density_xy(colapm_ctx* c) {
     Phase ph(c, COLAPM_PHASE_FFT_FWD);
     float2* d = reinterpret_cast<float2*>(c->F);
+    c->rho_clean = false;
     if (use_xy(c, 1)) {
-        CKL(launch_xy_fwd(c->nm, c->rho, d, c->tw_m, density_scale(c), c->xy_ring, c->xy_ctr, c->err, c->stream));
+        CKL(launch_xy_fwd(c->nm, c->rho, d, c->tw_m, density_scale(c), c->xy_ring, c->xy_ctr, c->err, c->stream, true));
+        c->rho_clean = true;
         return COLAPM_OK;
     }
-    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, c->two_stage));
+    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, c->two_stage, true));
+    c->rho_clean = true;
     CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream, c->two_stage));
     return COLAPM_OK;
 }

@@ -63,8 +63,9 @@ __device__ __forceinline__ int power_bin(int n2, const int* lo, int nbins) {
 // when a cell has its top bit set); in_f32: real field.
 // `two_stage` selects the two-stage register FFT where it exists (256, 512, 1024 lines); the
 // shared-memory Stockham kernels otherwise.
+// zero_input: clear the int64 mesh as it is read, so that the next deposit needs no memset.
 cudaError_t launch_fx_fwd_i64(int n_mesh, const unsigned long long* in, float2* out, const float2* tw,
-                              float scale, int* err, cudaStream_t s, bool two_stage = true);
+                              float scale, int* err, cudaStream_t s, bool two_stage = true, bool zero_input = false);
 cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const float2* tw, cudaStream_t s,
                               bool two_stage = true);
 // Inverse x pass (c2r), in place, for `nfields` arrays spaced `field_stride` complex apart.
@@ -81,7 +82,7 @@ bool xy_supported(int nm);
 size_t xy_ring_bytes(int nm);
 size_t xy_ctr_ints(int nm, int nfields);
 cudaError_t launch_xy_fwd(int nm, const unsigned long long* rho, float2* out, const float2* tw, float scale,
-                          float2* ring, int* ctr, int* err, cudaStream_t s);
+                          float2* ring, int* ctr, int* err, cudaStream_t s, bool zero_input = false);
 cudaError_t launch_xy_inv(int nm, float2* data, size_t fstride, int nfields, const float2* tw, float2* ring, int* ctr,
                           int* err, cudaStream_t s);
 

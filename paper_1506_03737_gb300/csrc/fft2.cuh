@@ -32,11 +32,11 @@ template <> struct F2<1024> { static constexpr int R1 = 32, R2 = 32; };
 template <int L>
 struct F2Has { static constexpr bool value = L == 256 || L == 512 || L == 1024; };
 
-// Exchange buffer of 8 lines for a stage-A radix RA.
-template <int L, int RA>
+// Exchange buffer of LINES lines (8 by default) for a stage-A radix RA.
+template <int L, int RA, int LINES = 8>
 struct Xch {
     static constexpr int PITCH = L + L / RA + 4;   // = 4 (mod 16) for the sizes above
-    static constexpr int SIZE = 8 * PITCH;         // float2 elements
+    static constexpr int SIZE = LINES * PITCH;     // float2 elements
     __device__ __forceinline__ static int at(int c, int e) { return c * PITCH + e + e / RA; }
 };
 
@@ -93,10 +93,10 @@ __device__ __forceinline__ int sbin(int i, int L) { return i < L / 2 ? i : i - L
 
 // Stage B of a line held in exchange buffer xb (stage-A radix RA), task j < RA of line c:
 // loads j + RA r, twiddles, RB-point DFT. Returns X[j + RA r] in v.
-template <int L, int RA, int RB, int S>
+template <int L, int RA, int RB, int S, int LINES = 8>
 __device__ __forceinline__ void stage_b(const float2* xb, const Tw2* tw, int c, int j, float2* v) {
 #pragma unroll
-    for (int r = 0; r < RB; ++r) v[r] = xb[Xch<L, RA>::at(c, j + RA * r)];
+    for (int r = 0; r < RB; ++r) v[r] = xb[Xch<L, RA, LINES>::at(c, j + RA * r)];
     twiddle2<RB, S>(v, tw, j);
     dft<RB, S>(v);
 }
@@ -140,23 +140,25 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, siz
 // ---------------------------------------------------------------------------------------------
 // z pass with the spectral operator fused (see k_fz in fft_kernels.cuh for the algebra):
 // forward z (radices R1, R2) -> bases in registers -> inverse z (radices R2, R1) per base.
-template <int L, int MODE>
+// C columns per tile (8, or 4 to halve shared memory and fit two CTAs per SM).
+template <int L, int MODE, int C = 8>
 struct Z2 {
     static constexpr int R1 = F2<L>::R1, R2 = F2<L>::R2;
-    static constexpr int XS = Xch<L, R1>::SIZE > Xch<L, R2>::SIZE ? Xch<L, R1>::SIZE : Xch<L, R2>::SIZE;
+    static constexpr int XS = Xch<L, R1, C>::SIZE > Xch<L, R2, C>::SIZE ? Xch<L, R1, C>::SIZE : Xch<L, R2, C>::SIZE;
     static constexpr int NSAVE = MODE == Z_LPT1 ? 2 : (MODE == Z_POWER ? 0 : 1);   // saved bases B (, C)
     static constexpr bool PREFETCH = MODE != Z_LPT1;                              // next tile via cp.async
-    static constexpr int PF = PREFETCH ? 8 * L : 0;                               // dense [z][8] buffer
+    static constexpr int PF = PREFETCH ? C * L : 0;                               // dense [z][C] buffer
+    static constexpr int TA = C * L / R1, TB = C * L / R2, T = TA > TB ? TA : TB;
     static constexpr size_t SMEM = sizeof(float2) * ((size_t)XS * (1 + NSAVE) + PF) + sizeof(Tw2);
 };
 
-template <int L, int MODE>
-__global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut out, const float2* __restrict__ tw,
-                                                   const float* __restrict__ sinc2, int deconv, float gnorm,
-                                                   PowerArgs pw) {
-    using Z = Z2<L, MODE>;
-    constexpr int R1 = Z::R1, R2 = Z::R2, n = L / 2, NG = n / 8, NTILE = NG * L;
-    constexpr int T = K2<L>::T;
+template <int L, int MODE, int C = 8>
+__global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ in, ZOut out, const float2* __restrict__ tw,
+                                                          const float* __restrict__ sinc2, int deconv, float gnorm,
+                                                          PowerArgs pw) {
+    using Z = Z2<L, MODE, C>;
+    constexpr int R1 = Z::R1, R2 = Z::R2, n = L / 2, NG = n / C, NTILE = NG * L;
+    constexpr int T = Z::T;
     extern __shared__ float4 smem4[];
     float2* xb = reinterpret_cast<float2*>(smem4);
     float2* save = xb + Z::XS;                                   // bases B (, C), layout Xch<L,R1>
@@ -178,13 +180,14 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
     __syncthreads();
     const float kf = 6.283185307179586f / (float)L;
     const size_t stride = (size_t)L * n;
-    const int tid = threadIdx.x, c = tid & 7, j = tid >> 3;
-    constexpr int TA = 8 * L / R1, TB = 8 * L / R2;   // forward stage-A / stage-B tasks
-    auto prefetch = [&](int tt) {   // 16-byte cp.async.cg of rows z = 0..L-1, 8 columns, into pf
-        const size_t b = (size_t)(tt / NG) * n + (tt % NG) * 8;
-        for (int e = tid; e < L * 4; e += T) {
-            const int z = e >> 2, q = e & 3;
-            cp_async16_cg(pf + z * 8 + 2 * q, in + b + (size_t)z * stride + 2 * q);
+    const int tid = threadIdx.x, c = tid % C, j = tid / C;
+    constexpr int TA = Z::TA, TB = Z::TB;   // forward stage-A / stage-B tasks
+    auto prefetch = [&](int tt) {   // 16-byte cp.async.cg of rows z = 0..L-1, C columns, into pf
+        const size_t b = (size_t)(tt / NG) * n + (tt % NG) * C;
+        constexpr int Q = C / 2;    // 16-byte pieces per row
+        for (int e = tid; e < L * Q; e += T) {
+            const int z = e / Q, q = e % Q;
+            cp_async16_cg(pf + z * C + 2 * q, in + b + (size_t)z * stride + 2 * q);
         }
         cp_async_commit();
     };
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
     }
 
     for (int t = blockIdx.x; t < NTILE; t += gridDim.x) {
-        const int ky = t / NG, kx0 = (t % NG) * 8;
+        const int ky = t / NG, kx0 = (t % NG) * C;
         const int ny = sbin(ky, L);
         const bool nyq_y = (ky == L / 2);
         const size_t base = (size_t)ky * n + kx0 + c;
@@ -210,17 +213,17 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
             float2 a[R1];
             if (tid < TA) {
 #pragma unroll
-                for (int r = 0; r < R1; ++r) a[r] = pf[(j + r * (L / R1)) * 8 + c];
+                for (int r = 0; r < R1; ++r) a[r] = pf[(j + r * (L / R1)) * C + c];
             }
             __syncthreads();   // prefetch buffer consumed
             if (t + (int)gridDim.x < NTILE) prefetch(t + gridDim.x);
             if (tid < TA) {
                 dft<R1, -1>(a);
 #pragma unroll
-                for (int r = 0; r < R1; ++r) xb[Xch<L, R1>::at(c, j * R1 + r)] = a[r];
+                for (int r = 0; r < R1; ++r) xb[Xch<L, R1, C>::at(c, j * R1 + r)] = a[r];
             }
             __syncthreads();
-            if (tid < TB) stage_b<L, R1, R2, -1>(xb, tws, c, j, v);
+            if (tid < TB) stage_b<L, R1, R2, -1, C>(xb, tws, c, j, v);
         }
 
         if constexpr (MODE == Z_POWER) {
@@ -228,11 +231,11 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
             // consecutive z of one column, flushing when the bin changes.
             if (tid < TB) {
 #pragma unroll
-                for (int r = 0; r < R2; ++r) xb[Xch<L, R1>::at(c, j + R1 * r)] = v[r];
+                for (int r = 0; r < R2; ++r) xb[Xch<L, R1, C>::at(c, j + R1 * r)] = v[r];
             }
             __syncthreads();
-            constexpr int PER = L * 8 / T;
-            const int pc = tid % 8, z0 = (tid / 8) * PER, px = kx0 + pc;
+            constexpr int PER = L * C / T;
+            const int pc = tid % C, z0 = (tid / C) * PER, px = kx0 + pc;
             if (!nyq_y) {
                 int rb = -1;
                 double rp = 0.0, rk = 0.0;   // FP64 sums of FP32 per-mode values
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
                         rk = 0.0;
                         rc = 0;
                     }
-                    const float2 q = xb[Xch<L, R1>::at(pc, z)];
+                    const float2 q = xb[Xch<L, R1, C>::at(pc, z)];
                     const float w = sinc2[px] * sinc2[ky] * sinc2[z];
                     rp += (double)(mult * (q.x * q.x + q.y * q.y) * pw.pnorm / (w * w));
                     rk += (double)(mult * pw.kf * sqrtf((float)n2));
@@ -290,8 +293,8 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
                     }
                     v[r] = cscale(v[r], g);
                     const float kz = kf * (float)nz;
-                    save[Xch<L, R1>::at(c, j + R1 * r)] = cscale(v[r], kz);
-                    if constexpr (Z::NSAVE == 2) save[Z::XS + Xch<L, R1>::at(c, j + R1 * r)] = cscale(v[r], kz * kz);
+                    save[Xch<L, R1, C>::at(c, j + R1 * r)] = cscale(v[r], kz);
+                    if constexpr (Z::NSAVE == 2) save[Z::XS + Xch<L, R1, C>::at(c, j + R1 * r)] = cscale(v[r], kz * kz);
                 }
             }
             __syncthreads();   // forward exchange buffer free
@@ -305,16 +308,16 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fz(float2* __restrict__ in, ZOut 
                 if (tid < TB) {
                     if (bi > 0) {
 #pragma unroll
-                        for (int r = 0; r < R2; ++r) v[r] = save[(bi - 1) * Z::XS + Xch<L, R1>::at(c, j + R1 * r)];
+                        for (int r = 0; r < R2; ++r) v[r] = save[(bi - 1) * Z::XS + Xch<L, R1, C>::at(c, j + R1 * r)];
                     }
                     dft<R2, +1>(v);
 #pragma unroll
-                    for (int r = 0; r < R2; ++r) xb[Xch<L, R2>::at(c, j * R2 + r)] = v[r];
+                    for (int r = 0; r < R2; ++r) xb[Xch<L, R2, C>::at(c, j * R2 + r)] = v[r];
                 }
                 __syncthreads();
                 if (tid < TA) {   // inverse stage B (radix R1), task j < R2: outputs at j + R2 r
                     float2 u[R1];
-                    stage_b<L, R2, R1, +1>(xb, tws, c, j, u);
+                    stage_b<L, R2, R1, +1, C>(xb, tws, c, j, u);
 #pragma unroll
                     for (int r = 0; r < R1; ++r) {
                         const size_t o = base + (size_t)(j + R2 * r) * stride;
@@ -367,10 +370,11 @@ struct X2 {
 };
 
 // forward r2c: in = int64 density pairs (I64, converted to rho * scale - 1) or float reals.
+// zero (optional): the int64 input itself, cleared as it is read (the next deposit then needs no memset).
 template <int n, bool I64>
 __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ in_, float2* __restrict__ out,
                                                        const float2* __restrict__ tw, float scale, int* err,
-                                                       int nitems) {
+                                                       int nitems, unsigned long long* zero) {
     using X = X2<n>;
     constexpr int RA = X::RA, RB = X::RB, N = 2 * n;
     extern __shared__ float4 smem4[];
@@ -385,16 +389,25 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ i
         if (tid < X::TA) {   // stage A: line c, task j (j fastest)
             const int c = tid / (n / RA), j = tid % (n / RA);
             float2 v[RA];
+            if constexpr (I64) {
+                // all loads first: the clearing stores go through another pointer to the same memory
+                ulonglong2 q[RA];
 #pragma unroll
-            for (int r = 0; r < RA; ++r) {
-                const size_t g = (row0 + c) * n + j + r * (n / RA);
-                if constexpr (I64) {
-                    const ulonglong2 q = __ldcs(reinterpret_cast<const ulonglong2*>(in_) + g);
-                    over |= ((q.x | q.y) >> 63) != 0;
-                    v[r] = make_float2(fmaf((float)(long long)q.x, scale, -1.0f), fmaf((float)(long long)q.y, scale, -1.0f));
-                } else {
-                    v[r] = __ldcg(reinterpret_cast<const float2*>(in_) + g);
+                for (int r = 0; r < RA; ++r) q[r] = __ldcs(reinterpret_cast<const ulonglong2*>(in_) + (row0 + c) * n + j + r * (n / RA));
+                if (zero) {
+#pragma unroll
+                    for (int r = 0; r < RA; ++r)
+                        __stcs(reinterpret_cast<ulonglong2*>(zero) + (row0 + c) * n + j + r * (n / RA), make_ulonglong2(0ull, 0ull));
                 }
+#pragma unroll
+                for (int r = 0; r < RA; ++r) {
+                    over |= ((q[r].x | q[r].y) >> 63) != 0;
+                    v[r] = make_float2(fmaf((float)(long long)q[r].x, scale, -1.0f),
+                                       fmaf((float)(long long)q[r].y, scale, -1.0f));
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < RA; ++r) v[r] = __ldcg(reinterpret_cast<const float2*>(in_) + (row0 + c) * n + j + r * (n / RA));
             }
             dft<RA, -1>(v);
 #pragma unroll

@@ -144,7 +144,7 @@ struct FxFwd {
 template <int n, bool I64>
 __global__ void __launch_bounds__(XT<n>::T) k_fx_fwd(const void* __restrict__ in_, float2* __restrict__ out,
                                                       const float2* __restrict__ tw, float scale, int* err,
-                                                      int nitems) {
+                                                      int nitems, unsigned long long* zero) {
     using C = FxFwd<n, I64>;
     constexpr int T = C::T, N = C::N, ESZ = I64 ? 16 : 8;
     extern __shared__ float4 smem4[];
@@ -165,6 +165,10 @@ __global__ void __launch_bounds__(XT<n>::T) k_fx_fwd(const void* __restrict__ in
         cp_async_wait<1>();
         __syncthreads();
         if constexpr (I64) {
+            if (zero) {   // the staged rows of tile t are in shared memory: clear them in the input
+                ulonglong2* z = reinterpret_cast<ulonglong2*>(zero) + (size_t)t * 8 * n;
+                for (int e = threadIdx.x; e < n * 8; e += T) __stcs(z + e, make_ulonglong2(0ull, 0ull));
+            }
             const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(stg);
             for (int e = threadIdx.x; e < n * 8; e += T) {
                 const int c = e & 7, p = e >> 3;

@@ -6,7 +6,7 @@ namespace colapm {
 
 template <int N, bool I64>
 static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float scale, int* err, cudaStream_t s,
-                            bool two_stage) {
+                            bool two_stage, unsigned long long* zero = nullptr) {
     constexpr int n = N / 2;
     if constexpr (F2Has<n>::value) if (two_stage) {
         using X = X2<n>;
@@ -17,7 +17,7 @@ static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float
             grid2 = persistent_grid(k2_fx_fwd<n, I64>, X::T, X::SMEM);
         }
         const int items = N * N / 8;
-        k2_fx_fwd<n, I64><<<grid2 < items ? grid2 : items, X::T, X::SMEM, s>>>(in, out, tw, scale, err, items);
+        k2_fx_fwd<n, I64><<<grid2 < items ? grid2 : items, X::T, X::SMEM, s>>>(in, out, tw, scale, err, items, zero);
         return cudaGetLastError();
     }
     using C = FxFwd<n, I64>;
@@ -28,7 +28,7 @@ static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float
         grid = persistent_grid(k_fx_fwd<n, I64>, C::T, C::SMEM);
     }
     const int items = N * N / 8;
-    k_fx_fwd<n, I64><<<grid < items ? grid : items, C::T, C::SMEM, s>>>(in, out, tw, scale, err, items);
+    k_fx_fwd<n, I64><<<grid < items ? grid : items, C::T, C::SMEM, s>>>(in, out, tw, scale, err, items, zero);
     return cudaGetLastError();
 }
 
@@ -61,9 +61,10 @@ static cudaError_t fx_inv_t(float2* data, size_t fstride, int nfields, const flo
 }
 
 cudaError_t launch_fx_fwd_i64(int n_mesh, const unsigned long long* in, float2* out, const float2* tw,
-                              float scale, int* err, cudaStream_t s, bool two_stage) {
+                              float scale, int* err, cudaStream_t s, bool two_stage, bool zero_input) {
+    unsigned long long* z = zero_input ? const_cast<unsigned long long*>(in) : nullptr;
     switch (n_mesh) {
-#define X(N) case N: return fx_fwd_t<N, true>(in, out, tw, scale, err, s, two_stage);
+#define X(N) case N: return fx_fwd_t<N, true>(in, out, tw, scale, err, s, two_stage, z);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;

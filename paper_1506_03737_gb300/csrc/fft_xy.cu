@@ -125,18 +125,26 @@ __device__ __forceinline__ void y_tile(const float2* __restrict__ src, float2* _
 // of n complex (k_x < n; the k_x = n plane is dropped, as every spectral operator zeroes it).
 template <int n>
 __device__ __forceinline__ bool x_fwd_rows(const unsigned long long* __restrict__ rho, float2* __restrict__ out,
-                                           const float2* __restrict__ tw, float scale, float2* xb, const Tw2* tws) {
+                                           const float2* __restrict__ tw, float scale, float2* xb, const Tw2* tws,
+                                           bool zero) {
     constexpr int RA = F2<n>::R1, RB = F2<n>::R2, TA = 8 * n / RA, TB = 8 * n / RB;
     const int tid = threadIdx.x;
     bool over = false;
     if (tid < TA) {
         const int c = tid / (n / RA), j = tid % (n / RA);
         float2 v[RA];
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rho) + (size_t)c * n + j;
+        ulonglong2 q[RA];   // all loads first: the clearing stores alias them
+#pragma unroll
+        for (int r = 0; r < RA; ++r) q[r] = __ldcs(src + r * (n / RA));
+        if (zero) {
+#pragma unroll
+            for (int r = 0; r < RA; ++r) __stcs(const_cast<ulonglong2*>(src) + r * (n / RA), make_ulonglong2(0ull, 0ull));
+        }
 #pragma unroll
         for (int r = 0; r < RA; ++r) {
-            const ulonglong2 q = __ldcs(reinterpret_cast<const ulonglong2*>(rho) + (size_t)c * n + j + r * (n / RA));
-            over |= ((q.x | q.y) >> 63) != 0;
-            v[r] = make_float2(fmaf((float)(long long)q.x, scale, -1.0f), fmaf((float)(long long)q.y, scale, -1.0f));
+            over |= ((q[r].x | q[r].y) >> 63) != 0;
+            v[r] = make_float2(fmaf((float)(long long)q[r].x, scale, -1.0f), fmaf((float)(long long)q[r].y, scale, -1.0f));
         }
         dft<RA, -1>(v);
 #pragma unroll
@@ -289,7 +297,8 @@ __global__ void __launch_bounds__(XY_T, 2) k_xy_inv(float2* __restrict__ data, s
 template <int L>
 __global__ void __launch_bounds__(XY_T, 2) k_xy_fwd(const unsigned long long* __restrict__ rho, float2* __restrict__ out,
                                                      const float2* __restrict__ tw, float scale,
-                                                     float2* __restrict__ ring, int* __restrict__ ctr, int* err) {
+                                                     float2* __restrict__ ring, int* __restrict__ ctr, int* err,
+                                                     bool zero) {
     using P = XY<L>;
     extern __shared__ float4 smem4[];
     __shared__ int tk;
@@ -319,7 +328,7 @@ __global__ void __launch_bounds__(XY_T, 2) k_xy_fwd(const unsigned long long* __
                 if (u >= XY_RING) wait_count(done2 + (u - XY_RING), P::COLS, err);
                 const size_t row0 = (size_t)u * L + 8 * k;   // density rows of N = L values
                 over |= x_fwd_rows<P::n>(rho + row0 * L, ring + (size_t)(u % XY_RING) * P::PLANE + (size_t)8 * k * P::n,
-                                         tw, scale, xb, twx);
+                                         tw, scale, xb, twx, zero);
                 done = done1 + u;
             }
         } else {
@@ -360,17 +369,17 @@ size_t xy_ring_bytes(int nm) { return xy_supported(nm) ? (size_t)XY_RING * nm * 
 size_t xy_ctr_ints(int nm, int nfields) { return 1 + 2 * (size_t)nm * nfields; }
 
 cudaError_t launch_xy_fwd(int nm, const unsigned long long* rho, float2* out, const float2* tw, float scale,
-                          float2* ring, int* ctr, int* err, cudaStream_t s) {
+                          float2* ring, int* ctr, int* err, cudaStream_t s, bool zero_input) {
     cudaError_t e = cudaMemsetAsync(ctr, 0, xy_ctr_ints(nm, 1) * sizeof(int), s);
     if (e) return e;
     switch (nm) {
     case 512:
         k_xy_fwd<512><<<xy_grid((const void*)k_xy_fwd<512>, XY<512>::SMEM, &g_fwd512), XY_T, XY<512>::SMEM, s>>>(
-            rho, out, tw, scale, ring, ctr, err);
+            rho, out, tw, scale, ring, ctr, err, zero_input);
         break;
     case 1024:
         k_xy_fwd<1024><<<xy_grid((const void*)k_xy_fwd<1024>, XY<1024>::SMEM, &g_fwd1024), XY_T, XY<1024>::SMEM, s>>>(
-            rho, out, tw, scale, ring, ctr, err);
+            rho, out, tw, scale, ring, ctr, err, zero_input);
         break;
     default: return cudaErrorInvalidValue;
     }

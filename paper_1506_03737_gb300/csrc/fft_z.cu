@@ -8,18 +8,19 @@ template <int N, int MODE>
 static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm,
                            PowerArgs pw, cudaStream_t s, bool two_stage) {
     if constexpr (F2Has<N>::value) if (two_stage) {
-        using Z = Z2<N, MODE>;
+        constexpr int CZ = 8;   // 4-column tiles fit two CTAs per SM but measured slower (32-byte rows)
+        using Z = Z2<N, MODE, CZ>;
         const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
         static size_t configured2 = 0;
         static int grid2 = 0;
         if (smem > configured2 || !grid2) {
-            cudaError_t e = set_smem(k2_fz<N, MODE>, smem);
+            cudaError_t e = set_smem(k2_fz<N, MODE, CZ>, smem);
             if (e != cudaSuccess) return e;
             configured2 = smem > configured2 ? smem : configured2;
-            grid2 = persistent_grid(k2_fz<N, MODE>, K2<N>::T, smem);
+            grid2 = persistent_grid(k2_fz<N, MODE, CZ>, Z::T, smem);
         }
-        const int total = (N / 2 / 8) * N;
-        k2_fz<N, MODE><<<grid2 < total ? grid2 : total, K2<N>::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
+        const int total = (N / 2 / CZ) * N;
+        k2_fz<N, MODE, CZ><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
         return cudaGetLastError();
     }
     using C = Fz<N, MODE>;
