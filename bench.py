@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 from paper_1506_03737_gb300 import workloads  # noqa: E402
 
-# Algorithmic bytes (minimum HBM traffic) per COLA step, per the layout in the design doc:
+# Algorithmic bytes (minimum HBM traffic) per COLA step for this data layout:
 # particles 96 B per particle-update; mesh 80 B per cell.
 ALG_BYTES_PARTICLE = 96
 ALG_BYTES_CELL = 80
@@ -375,6 +375,9 @@ def main():
     if dom == "gather":
         nbytes += 12 * nm ** 3
     achieved = nbytes / (per_call[dom] / 1e3) / 1e9
+    # DRAM bytes (read + write) per cell of the force z pass from an ncu capture of the same
+    # kernel at 512^3 (537.0 MB + 1556.3 MB), scaled by the cell count; none for the gather.
+    traffic = 2093.3e6 / 512 ** 3 * nm ** 3 if dom == "poisson" else None
     alg_step = ALG_BYTES_PARTICLE * np_ ** 3 + ALG_BYTES_CELL * nm ** 3
 
     line = {
@@ -388,7 +391,7 @@ def main():
                    "l2": "inputs larger than L2 (particle state and meshes ~35 GB)"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": f"{peak_src} hbm_gbs"},
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs"},
         "cola_step_ms": sum(phase_ms[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "gather"))
                         / max(int(phase_n["gather"]), 1),
         "cola_step_roofline_frac": None,

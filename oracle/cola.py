@@ -28,7 +28,9 @@ class Run:
     """State of one simulation in the oracle (all FP64, particle-id order)."""
 
     def __init__(self, box, np_, nm, om, z_init, z_final, n_steps, spacing="lin",
-                 stepping="modified", nlpt=-2.5, cola=True, deconv=1):
+                 stepping="modified", nlpt=-2.5, cola=True, deconv=1, fft=None):
+        """fft="numpy": numpy's FFT as the transform primitive (large meshes); same operators."""
+        self.fft = fft
         self.box, self.np_, self.nm = float(box), int(np_), int(nm)
         self.om, self.cola, self.deconv = float(om), bool(cola), int(deconv)
         self.table = cosmology.timestep_table(om, z_init, z_final, n_steps, spacing, stepping, nlpt)
@@ -52,13 +54,13 @@ class Run:
 
     def make_ics(self, seed, pk):
         delta_k = ics.gaussian_field(self.np_, self.box, seed, pk)
-        psi1, psi2 = ics.lpt_displacements(delta_k, self.box)
+        psi1, psi2 = ics.lpt_displacements(delta_k, self.box, self.fft)
         self.set_displacements(psi1, psi2)
         return delta_k
 
     # --- one Kick-Drift step ------------------------------------------------------------
     def force(self):
-        f, _ = pm.pm_accel(self.x, self.box, self.np_, self.nm, self.deconv)
+        f, _ = pm.pm_accel(self.x, self.box, self.np_, self.nm, self.deconv, self.fft)
         return f
 
     def kick(self, coeff, d1, d2, force):

@@ -92,8 +92,11 @@ def gaussian_field(n, box, seed, pk):
     return full
 
 
-def lpt_displacements(delta_k, box):
-    """Return (Psi1, Psi2), each (3, N, N, N) real [component x,y,z][iz][iy][ix], in Mpc/h."""
+def lpt_displacements(delta_k, box, fft=None):
+    """Return (Psi1, Psi2), each (3, N, N, N) real [component x,y,z][iz][iy][ix], in Mpc/h.
+
+    fft="numpy" takes numpy's FFT as the transform primitive (large grids); the operators are the same."""
+    fftn_, ifftn_ = (np.fft.fftn, np.fft.ifftn) if fft == "numpy" else (fftn, ifftn)
     kx, ky, kz, nyq = wavevectors(delta_k.shape[0], box)
     kvec = (kx, ky, kz)
     k2 = kx * kx + ky * ky + kz * kz
@@ -101,15 +104,15 @@ def lpt_displacements(delta_k, box):
     ok = (k2 > 0) & ~nyq
     inv[ok] = 1.0 / k2[ok]
 
-    psi1 = np.stack([ifftn(1j * kvec[j] * delta_k * inv).real for j in range(3)])
+    psi1 = np.stack([ifftn_(1j * kvec[j] * delta_k * inv).real for j in range(3)])
     phi = {}
     for a in range(3):
         for b in range(a, 3):
-            phi[a, b] = ifftn(kvec[a] * kvec[b] * delta_k * inv).real
+            phi[a, b] = ifftn_(kvec[a] * kvec[b] * delta_k * inv).real
     src = (phi[0, 0] * phi[1, 1] + phi[0, 0] * phi[2, 2] + phi[1, 1] * phi[2, 2]
            - phi[0, 1] ** 2 - phi[0, 2] ** 2 - phi[1, 2] ** 2)
-    src_k = fftn(src)
-    psi2 = np.stack([ifftn(-1j * kvec[j] * src_k * inv).real for j in range(3)])
+    src_k = fftn_(src)
+    psi2 = np.stack([ifftn_(-1j * kvec[j] * src_k * inv).real for j in range(3)])
     return psi1, psi2
 
 

@@ -128,9 +128,9 @@ def cic_gather(force, u):
     return out
 
 
-def pm_accel(x, box, np_, nm, deconv=1):
+def pm_accel(x, box, np_, nm, deconv=1, fft=None):
     """Mesh force F (Mpc/h) at particle positions x (Mpc/h, (P,3)), and the int64 density used."""
     u = np.mod(np.asarray(x, dtype=np.float64) * (nm / box), nm)
     rho = cic_deposit(u, nm)
-    force = force_mesh(density_contrast(rho, np_, nm), box, deconv)
+    force = force_mesh(density_contrast(rho, np_, nm), box, deconv, fft)
     return cic_gather(force, u) , rho

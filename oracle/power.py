@@ -53,13 +53,15 @@ def binned_power(delta_k, box, nbins, kmin, kmax, window=True):
         return ksum / cnt, psum / cnt, cnt
 
 
-def power_from_positions(x, box, np_, nm, nbins=100, kmin=None, kmax=None):
-    """Deposit, transform and bin (defaults: kmin = 2 pi / L, kmax = pi N_m / L)."""
+def power_from_positions(x, box, np_, nm, nbins=100, kmin=None, kmax=None, fft=None):
+    """Deposit, transform and bin (defaults: kmin = 2 pi / L, kmax = pi N_m / L); fft="numpy" takes
+    numpy's FFT as the transform primitive."""
     kmin = 2.0 * math.pi / box if kmin is None else kmin
     kmax = math.pi * nm / box if kmax is None else kmax
     u = np.mod(np.asarray(x, dtype=np.float64) * (nm / box), nm)
     rho = pm.cic_deposit(u, nm)
-    dk = fftn(pm.density_contrast(rho, np_, nm))
+    delta = pm.density_contrast(rho, np_, nm)
+    dk = np.fft.fftn(delta) if fft == "numpy" else fftn(delta)
     return binned_power(dk, box, nbins, kmin, kmax)
 
 

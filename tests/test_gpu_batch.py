@@ -94,3 +94,36 @@ def test_autotune_preserves_state_and_results(C):
     finally:
         C.colapm_destroy(a)
         C.colapm_destroy(b)
+
+
+def test_uneven_batch_mocks_match_oracle_at_full_size(C):
+    """Mocks r = 0..7 of the 64-mock uneven batch (N_p = 64 + 32 (r mod 5), N_m = 2 N_p,
+    L = 128 + 96 (r mod 5) Mpc/h, seed 1000 + r, 10 steps): every mock equals a single context,
+    and the two the FP64 oracle runs in under a minute (r = 0, 1) match it within 0.1% per bin."""
+    params = []
+    for r in range(8):
+        k = r % 5
+        npp = 64 + 32 * k
+        params.append(C.default_params(np=npp, nm=2 * npp, box=128.0 + 96.0 * k, seed=1000 + r))
+    b = C.colapm_batch_create(params, nstreams=0)
+    try:
+        nbins = 100
+        kb, pb, nb = C.colapm_batch_run(b, len(params), nbins)
+    finally:
+        C.colapm_batch_destroy(b)
+    for i, prm in enumerate(params[:5]):          # the five distinct sizes
+        ks, ps, ns = single_power(C, prm, nbins)
+        assert np.array_equal(nb[i], ns)
+        ok = ns > 0
+        assert np.max(np.abs(pb[i][ok] / ps[ok] - 1)) < 1e-9
+    pk = ocosmo.linear_pk(0.3, 0.7, 0.96, 0.8)
+    for i in (0, 1):
+        prm = params[i]
+        r = ocola.Run(prm.box, prm.np, prm.nm, 0.3, 9.0, 0.0, 10, fft="numpy")
+        r.make_ics(prm.seed, pk)
+        r.run()
+        kr, pr, nr = opower.power_from_positions(r.x, prm.box, prm.np, prm.nm, nbins, fft="numpy")
+        assert np.array_equal(nb[i], nr)
+        ok = nr > 0
+        assert np.max(np.abs(pb[i][ok] / pr[ok] - 1)) < 1e-3
+        assert np.max(np.abs(kb[i][ok] / kr[ok] - 1)) < 1e-6

@@ -278,3 +278,18 @@ def test_planar_force_reduces_the_3d_operator_to_one_axis():
     # numpy's FFT as the primitive gives the same operator
     delta = rng.standard_normal((nm, nm, nm))
     assert np.allclose(opm.force_mesh(delta, box, 1, fft="numpy"), opm.force_mesh(delta, box, 1), atol=1e-10)
+
+
+def test_numpy_fft_primitive_gives_the_same_run():
+    # The fft="numpy" option swaps only the transform primitive: same ICs, steps and P(k).
+    kw = dict(box=64.0, np_=8, nm=16, om=0.3, z_init=9.0, z_final=0.0, n_steps=3)
+    pk = cosmology.linear_pk(0.3, 0.7, 0.96, 0.8)
+    a, b = cola.Run(**kw), cola.Run(**kw, fft="numpy")
+    a.make_ics(5, pk)
+    b.make_ics(5, pk)
+    a.run()
+    b.run()
+    assert np.max(np.abs(a.x - b.x)) < 1e-9
+    pa = power.power_from_positions(a.x, 64.0, 8, 16, 8)
+    pb = power.power_from_positions(b.x, 64.0, 8, 16, 8, fft="numpy")
+    assert np.allclose(pa[1], pb[1], rtol=1e-9, equal_nan=True)
