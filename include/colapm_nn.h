@@ -39,10 +39,12 @@ typedef struct colapm_nn colapm_nn;
 typedef struct {
     float s_in, s_out;            /* input and output scales, Mpc/h (> 0)                        */
     float lr, beta1, beta2, eps;  /* Adam (Kingma & Ba 2015) step size and moment constants      */
+    int engine;                   /* convolutions: 0 mma.sync (default); 1 tcgen05 tensor cores   */
+                                  /* where n % 128 == 0 (mma.sync otherwise)                      */
     unsigned long long seed;      /* He-normal initial weights (splitmix64 + Box-Muller); b = 0  */
 } colapm_nn_config;
 
-/* s_in = s_out = 1, lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8, seed = 1. */
+/* s_in = s_out = 1, lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8, engine = 0, seed = 1. */
 void colapm_nn_default_config(colapm_nn_config* cfg);
 
 /* A network for n^3 fields (n a multiple of 16, 16..1024); allocates about 7 n^3 x 32 bytes of
@@ -67,7 +69,8 @@ int colapm_nn_grads(colapm_nn* nn, const float* psi, const float* target, float*
  * the update (synchronises when requested). */
 int colapm_nn_train_step(colapm_nn* nn, const float* psi, const float* target, double* loss);
 
-/* Adam steps taken; kernels launched by this network so far; wait for its stream. */
+/* Adam steps taken; kernels launched by this network so far; wait for its stream (and report
+ * COLAPM_E_TIMEOUT if a bounded device-side wait of a tensor-core convolution gave up). */
 int colapm_nn_steps(colapm_nn* nn);
 long long colapm_nn_launches(colapm_nn* nn);
 int colapm_nn_sync(colapm_nn* nn);

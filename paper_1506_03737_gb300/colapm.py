@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
 class NNConfig(ctypes.Structure):
     _fields_ = [("s_in", ctypes.c_float), ("s_out", ctypes.c_float), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("seed", ctypes.c_ulonglong)]
+                ("engine", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
 NN_PARAMS = 16467

@@ -11,8 +11,11 @@
 //   weights      bf16 [tap][c_out 16][c_in 16], tap = (dz+1) 9 + (dy+1) 3 + (dx+1)
 //   master       fp32 [layer][28][16][16]: taps 0..26 = W[tap][o][i], slot 27 holds the bias in i = 0
 //
-// Every convolution (forward of each layer, backward-data of layers 2..4) is one implicit
-// GEMM over a 16 x 8 x 8 voxel tile: M = 16 consecutive x voxels per mma, N = output channels,
+// Every convolution (forward of each layer, backward-data of layers 2..4) is one implicit GEMM:
+// with mma.sync (k_conv, the default) over a 16 x 8 x 8 voxel tile, or on the tcgen05 tensor cores
+// (k_conv_tc, engine 1, grid side a multiple of 128). With 16 channels each tcgen05.mma (M = 128
+// voxels, N = 16, K = 16) reads a 4 KB operand from shared memory for 65,536 FLOP, which bounds it
+// by shared-memory bandwidth; measured at 128^3 it is slower than the mma.sync kernel. mma.sync: M = 16 consecutive x voxels per mma, N = output channels,
 // K = 16 input channels per tap, 27 taps. The 18 x 10 x 10 halo tile of the input is staged in
 // shared memory with cp.async; each voxel's two 16-byte halves swap places on every other
 // group of four voxels so that ldmatrix reads are free of bank conflicts.
@@ -70,6 +73,7 @@ struct ConvArgs {
     const float* target;         // EPI_OUT training: [n^3][3] physical; normalised by tscale
     float tscale, gscale;        // gscale = 2 / (3 n^3)
     double* loss;                // sum of squared normalised errors
+    int* err;                    // bit 4: a bounded wait for the tensor cores gave up
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -293,6 +297,205 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The same convolution on the 5th-generation tensor cores (tcgen05), for grids whose side is a
+// multiple of 128. A CTA computes TC_ROWS output x-rows of 128 voxels; for each row and tap one
+// tcgen05.mma (M = 128 voxels, N = 16 output channels, K = 16 input channels, BF16 x BF16 -> FP32)
+// accumulates into the row's 16 TMEM columns. The halo is staged as two K-half planes (channels
+// 0..7 and 8..15, 16 bytes per voxel), which is the no-swizzle K-major core-matrix layout: 8
+// consecutive voxels x 16 bytes form one 128-byte core matrix, LBO = the plane distance (K),
+// SBO = 128 bytes (next 8 voxels). A tap's operand is the row of 128 halo voxels shifted by the
+// tap, i.e. a descriptor start offset. Weights: [tap][K half][16 outputs][8 inputs] (512 B a tap).
+// One thread issues the MMAs and commits them to an mbarrier; after a bounded wait the four warps
+// read their TMEM lanes (lane = voxel) with tcgen05.ld and run the same epilogues as k_conv.
+constexpr int TC_TY = 2, TC_TZ = 2, TC_ROWS = TC_TY * TC_TZ;
+constexpr int TC_HX = 130, TC_HY = TC_TY + 2, TC_HZ = TC_TZ + 2;
+constexpr int TC_HALO = TC_HX * TC_HY * TC_HZ;                    // 2080 voxels
+constexpr uint32_t TC_PLANE = TC_HALO * 16;                       // bytes per K-half plane
+constexpr uint32_t TC_W = 27 * 512;                               // weight bytes
+constexpr size_t TC_SMEM = 2 * (size_t)TC_PLANE + TC_W + 128;     // + mbarrier and TMEM address
+constexpr uint32_t TC_COLS = TC_ROWS * 16;                        // TMEM columns (power of two)
+constexpr long long TC_SPIN_LIMIT = 1ll << 24;
+// kind::f16 instruction descriptor: FP32 D (bits 4-5), BF16 A and B (bits 7-9, 10-12), both
+// K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);   // no swizzle, base offset 0
+}
+
+// Stage the halo of tile t (periodic) into the two K-half planes with 16-byte cp.async.
+__device__ __forceinline__ void tc_stage(uint32_t sbase, const __nv_bfloat16* __restrict__ in, int n, int t) {
+    const int txn = n / 128, tyn = n / TC_TY;
+    const int x0 = (t % txn) * 128, y0 = ((t / txn) % tyn) * TC_TY, z0 = (t / (txn * tyn)) * TC_TZ;
+#pragma unroll 1
+    for (int row = 0; row < TC_HY * TC_HZ; ++row) {
+        const int hy = row % TC_HY, hz = row / TC_HY;
+        int gy = y0 - 1 + hy, gz = z0 - 1 + hz;
+        gy += gy < 0 ? n : (gy >= n ? -n : 0);
+        gz += gz < 0 ? n : (gz >= n ? -n : 0);
+        const __nv_bfloat16* src = in + ((size_t)gz * n + gy) * n * C;
+        for (int j = threadIdx.x; j < 2 * TC_HX; j += 128) {
+            const int hx = j >> 1, k = j & 1;
+            int gx = x0 - 1 + hx;
+            gx += gx < 0 ? n : (gx >= n ? -n : 0);
+            cp_async16(sbase + k * TC_PLANE + (row * TC_HX + hx) * 16, src + (size_t)gx * C + k * 8);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+
+// Persistent over tiles: weights, TMEM and the mbarrier are set up once per CTA. Per tile: wait for
+// the staged halo, issue the 27 x TC_ROWS MMAs (one thread), wait for them, start staging the next
+// tile's halo (the MMAs no longer read shared memory), then read TMEM and write the outputs.
+template <int EPI>
+__global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t* wsm = sm + 2 * TC_PLANE;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(wsm + TC_W);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int n = a.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int txn = n / 128, tyn = n / TC_TY;
+    const int ntiles = txn * tyn * (n / TC_TZ);
+    const uint32_t sbase = smem_u32(sm);
+    for (int j = tid; j < 27 * C * 2; j += 128) {     // weights [tap][K half][out][8]
+        const int tap = j >> 5, o = (j >> 1) & 15, k = j & 1;
+        cp_async16(sbase + 2 * TC_PLANE + tap * 512 + k * 256 + o * 16, a.w + (tap * C + o) * C + k * 8);
+    }
+    if (blockIdx.x < ntiles) tc_stage(sbase, a.in, n, blockIdx.x);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(TC_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t taddr = *tslot;
+    const uint64_t a_desc0 = tc_desc(sbase, TC_PLANE, 128), b_desc0 = tc_desc(sbase + 2 * TC_PLANE, 256, 128);
+    bool ok = true;
+    double lsum = 0.0;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // the tensor cores read these bytes
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (tid == 0) {
+#pragma unroll 1
+            for (int r = 0; r < TC_ROWS; ++r) {
+                const int ry = r % TC_TY, rz = r / TC_TY;
+                // descriptor start addresses count 16-byte units: adding a voxel index moves by one voxel
+                const uint64_t arow = a_desc0 + (uint64_t)(((rz + 1) * TC_HY + (ry + 1)) * TC_HX + 1);
+#pragma unroll
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int off = (tap / 9 - 1) * TC_HY * TC_HX + ((tap / 3) % 3 - 1) * TC_HX + (tap % 3 - 1);
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + r * 16),
+                        "l"(arow + (uint64_t)(int64_t)off), "l"(b_desc0 + (uint64_t)(tap * 32)), "r"(TC_IDESC), "r"(tap));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(mbar))
+                         : "memory");
+        }
+        uint32_t done = 0;
+        for (long long i = 0; i < TC_SPIN_LIMIT && !done; ++i) {
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_u32(mbar)), "r"(it & 1)
+                : "memory");
+        }
+        if (!done) {
+            if (tid == 0 && a.err) atomicOr(a.err, 4);
+            ok = false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (!__syncthreads_and(done)) break;
+        if (t + (int)gridDim.x < ntiles) tc_stage(sbase, a.in, n, t + gridDim.x);   // overlaps the epilogue
+        const int x0 = (t % txn) * 128, y0 = ((t / txn) % tyn) * TC_TY, z0 = (t / (txn * tyn)) * TC_TZ;
+#pragma unroll 1
+        for (int r = 0; r < TC_ROWS; ++r) {
+            uint32_t q[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+                  "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+                : "r"(taddr + ((uint32_t)(32 * warp) << 16) + r * 16));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            const int ry = r % TC_TY, rz = r / TC_TY;
+            const size_t v = ((size_t)(z0 + rz) * n + (y0 + ry)) * n + x0 + 32 * warp + lane;
+            float acc[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = __uint_as_float(q[c]);
+            if (EPI == EPI_RELU || EPI == EPI_MASK) {
+                uint32_t pk[8];
+                if (EPI == EPI_MASK) {
+                    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + v * C);
+                    const uint4 m0 = mp[0], m1 = mp[1];
+                    const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(&mw[c]);
+                        const float v0 = __bfloat162float(mk.x) > 0.0f ? acc[2 * c] : 0.0f;
+                        const float v1 = __bfloat162float(mk.y) > 0.0f ? acc[2 * c + 1] : 0.0f;
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(v0, v1);
+                        pk[c] = *reinterpret_cast<const uint32_t*>(&b);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(fmaxf(acc[2 * c] + a.bias[2 * c], 0.0f),
+                                                                       fmaxf(acc[2 * c + 1] + a.bias[2 * c + 1], 0.0f));
+                        pk[c] = *reinterpret_cast<const uint32_t*>(&b);
+                    }
+                }
+                uint4* op = reinterpret_cast<uint4*>(a.out + v * C);
+                op[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                op[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            } else {   // EPI_OUT: channels 0..2
+                float dzv[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float val = acc[c] + a.bias[c];
+                    a.y[v * 3 + c] = (a.base ? a.base[v * 3 + c] : 0.0f) + a.oscale * val;
+                    dzv[c] = 0.0f;
+                    if (a.target) {
+                        const float d = val - a.target[v * 3 + c] * a.tscale;
+                        lsum += (double)d * d;
+                        dzv[c] = a.gscale * d;
+                    }
+                }
+                if (a.target) {
+                    const __nv_bfloat162 b01 = __floats2bfloat162_rn(dzv[0], dzv[1]);
+                    const __nv_bfloat162 b2z = __floats2bfloat162_rn(dzv[2], 0.0f);
+                    *reinterpret_cast<uint2*>(a.out + v * C) =
+                        make_uint2(*reinterpret_cast<const uint32_t*>(&b01), *reinterpret_cast<const uint32_t*>(&b2z));
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");   // TMEM reads done before the next MMAs
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (EPI == EPI_OUT && a.target) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if (lane == 0 && lsum != 0.0) atomicAdd(a.loss, lsum);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(TC_COLS));
+}
+
 __device__ __forceinline__ bool real_slot(int l, int slot, int o, int i) {
     constexpr int cin[LAYERS] = {3, 16, 16, 16}, cout[LAYERS] = {16, 16, 16, 3};
     if (o >= cout[l]) return false;
@@ -383,6 +586,9 @@ struct colapm_nn {
     __nv_bfloat16* wt = nullptr;
     float* bias = nullptr;             // [4][16]
     double* loss = nullptr;
+    int* err = nullptr;                // device error word (bit 4: a tensor-core wait gave up)
+    bool use_tc = false;               // tcgen05 convolutions (grid side a multiple of 128)
+    int tc_grid = 0;                   // persistent grid of the tcgen05 convolutions
     long long launches = 0;
 };
 
@@ -407,15 +613,39 @@ cudaError_t configure() {
     if ((e = cudaFuncSetAttribute(k_conv<2, EPI_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV))) return e;
     if ((e = cudaFuncSetAttribute(k_conv<1, EPI_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CONV))) return e;
     if ((e = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_WGRAD))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_tc<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_tc<EPI_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM))) return e;
+    if ((e = cudaFuncSetAttribute(k_conv_tc<EPI_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM))) return e;
     configured = true;
     return cudaSuccess;
 }
 
 template <int NT, int EPI>
-cudaError_t conv(colapm_nn* c, const ConvArgs& a) {
-    k_conv<NT, EPI><<<conv_grid(c->n), NTHREADS, SMEM_CONV, c->stream>>>(a);
+cudaError_t conv(colapm_nn* c, ConvArgs a) {
+    a.err = c->err;
+    if (c->use_tc) {
+        const int tiles = (c->n / 128) * (c->n / TC_TY) * (c->n / TC_TZ);
+        k_conv_tc<EPI><<<std::min(tiles, c->tc_grid), 128, TC_SMEM, c->stream>>>(a);
+    } else {
+        k_conv<NT, EPI><<<conv_grid(c->n), NTHREADS, SMEM_CONV, c->stream>>>(a);
+    }
     ++c->launches;
     return cudaGetLastError();
+}
+
+// Report (and clear) a device-side error of the network's kernels; synchronises.
+int check_err(colapm_nn* c) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return COLAPM_E_CUDA;
+    }
+    if (h) {
+        (void)cudaMemsetAsync(c->err, 0, sizeof(int), c->stream);
+        return COLAPM_E_TIMEOUT;
+    }
+    return COLAPM_OK;
 }
 
 // Weights (padded master layout) -> bf16 copies and bias, with no update.
@@ -549,6 +779,7 @@ void colapm_nn_default_config(colapm_nn_config* cfg) {
     cfg->beta1 = 0.9f;
     cfg->beta2 = 0.999f;
     cfg->eps = 1e-8f;
+    cfg->engine = 0;
     cfg->seed = 1;
 }
 
@@ -557,7 +788,7 @@ int colapm_nn_create(int n, const colapm_nn_config* cfg, void* stream, colapm_nn
     *out = nullptr;
     if (!cfg || n < 16 || n > 1024 || n % 16 != 0 || !(cfg->s_in > 0.0f) || !(cfg->s_out > 0.0f) ||
         !(cfg->lr >= 0.0f) || !(cfg->beta1 >= 0.0f && cfg->beta1 < 1.0f) || !(cfg->beta2 >= 0.0f && cfg->beta2 < 1.0f) ||
-        !(cfg->eps > 0.0f))
+        !(cfg->eps > 0.0f) || cfg->engine < 0 || cfg->engine > 1)
         return COLAPM_E_ARG;
     colapm_nn* c = new (std::nothrow) colapm_nn;
     if (!c) return COLAPM_E_NOMEM;
@@ -575,6 +806,9 @@ int colapm_nn_create(int n, const colapm_nn_config* cfg, void* stream, colapm_nn
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wgrad, NTHREADS, SMEM_WGRAD))
         return fail(COLAPM_E_CUDA);
     c->nparts = std::max(1, std::min(conv_grid(n), sms * std::max(occ, 1)));
+    int occ_tc = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_tc, k_conv_tc<EPI_RELU>, 128, TC_SMEM)) return fail(COLAPM_E_CUDA);
+    c->tc_grid = sms * std::max(occ_tc, 1);
     const size_t abytes = c->nv * C * sizeof(__nv_bfloat16);
     bool ok = true;
     for (int l = 0; l < LAYERS; ++l) ok = ok && cudaMalloc(&c->act[l], abytes) == cudaSuccess;
@@ -587,12 +821,14 @@ int colapm_nn_create(int n, const colapm_nn_config* cfg, void* stream, colapm_nn
          cudaMalloc(&c->wf, (size_t)LAYERS * 27 * C * C * sizeof(__nv_bfloat16)) == cudaSuccess &&
          cudaMalloc(&c->wt, (size_t)LAYERS * 27 * C * C * sizeof(__nv_bfloat16)) == cudaSuccess &&
          cudaMalloc(&c->bias, LAYERS * C * sizeof(float)) == cudaSuccess &&
-         cudaMalloc(&c->loss, sizeof(double)) == cudaSuccess;
+         cudaMalloc(&c->loss, sizeof(double)) == cudaSuccess && cudaMalloc(&c->err, sizeof(int)) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
         return fail(COLAPM_E_NOMEM);
     }
-    if (cudaMemsetAsync(c->dz_out, 0, abytes, c->stream) || cudaMemsetAsync(c->m1, 0, ps, c->stream) ||
+    c->use_tc = cfg->engine == 1 && n % 128 == 0;
+    if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) || cudaMemsetAsync(c->dz_out, 0, abytes, c->stream) ||
+        cudaMemsetAsync(c->m1, 0, ps, c->stream) ||
         cudaMemsetAsync(c->m2, 0, ps, c->stream) || cudaMemsetAsync(c->grad, 0, ps, c->stream))
         return fail(COLAPM_E_CUDA);
     std::vector<float> flat(COLAPM_NN_PARAMS);
@@ -615,6 +851,7 @@ int colapm_nn_destroy(colapm_nn* c) {
     cudaFree(c->wf);
     cudaFree(c->wt);
     cudaFree(c->loss);
+    cudaFree(c->err);
     (void)cudaGetLastError();
     delete c;
     return COLAPM_OK;
@@ -651,6 +888,7 @@ static int grads_impl(colapm_nn* c, const float* psi, const float* target, doubl
         NN_CK(cudaMemcpyAsync(&h, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         NN_CK(cudaStreamSynchronize(c->stream));
         *loss = h / (3.0 * (double)c->nv);
+        return check_err(c);
     }
     return COLAPM_OK;
 }
@@ -663,6 +901,7 @@ int colapm_nn_grads(colapm_nn* c, const float* psi, const float* target, float* 
         NN_CK(cudaMemcpyAsync(pad.data(), c->grad, pad.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
         NN_CK(cudaStreamSynchronize(c->stream));
         for_each_param([&](size_t k, size_t slot) { grads[k] = pad[slot]; });
+        return check_err(c);
     }
     return COLAPM_OK;
 }
@@ -683,6 +922,7 @@ int colapm_nn_train_step(colapm_nn* c, const float* psi, const float* target, do
         NN_CK(cudaMemcpyAsync(&h, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         NN_CK(cudaStreamSynchronize(c->stream));
         *loss = h / (3.0 * (double)c->nv);
+        return check_err(c);
     }
     return COLAPM_OK;
 }
@@ -693,8 +933,7 @@ long long colapm_nn_launches(colapm_nn* c) { return c ? c->launches : (long long
 
 int colapm_nn_sync(colapm_nn* c) {
     if (!c) return COLAPM_E_ARG;
-    NN_CK(cudaStreamSynchronize(c->stream));
-    return COLAPM_OK;
+    return check_err(c);
 }
 
 }  // extern "C"

@@ -50,6 +50,7 @@ def test_params_struct_and_defaults(lib):
 def test_nn_config_struct_and_defaults(lib):
     import ctypes
     c = lib.nn_default_config()
-    assert ctypes.sizeof(c) == 6 * 4 + 8
+    assert ctypes.sizeof(c) == 6 * 4 + 4 + 4 + 8          # int engine, padding, u64 seed
+    assert c.engine == 0
     assert (c.lr, c.beta1, c.eps, c.seed) == (np.float32(1e-3), np.float32(0.9), np.float32(1e-8), 1)
     assert lib.NN_PARAMS == 16467

@@ -46,8 +46,8 @@ def grid(a, n):
     return a.reshape(n, n, n, 3).astype(np.float64)
 
 
-def make_net(C, n, seed=1, lr=1e-3):
-    return C.colapm_nn_create(n, C.nn_default_config(s_in=S_IN, s_out=S_OUT, seed=seed, lr=lr))
+def make_net(C, n, seed=1, lr=1e-3, engine=0):
+    return C.colapm_nn_create(n, C.nn_default_config(s_in=S_IN, s_out=S_OUT, seed=seed, lr=lr, engine=engine))
 
 
 @pytest.mark.parametrize("n", [16, 48])
@@ -183,3 +183,57 @@ def test_rejects_bad_arguments(env):
             C.colapm_nn_forward(net, host, np.zeros_like(host))
     finally:
         C.colapm_nn_destroy(net)
+
+
+def test_tcgen05_forward_matches_oracle_on_sampled_blocks(env):
+    # engine 1 at n = 128 runs the convolutions on the tcgen05 tensor cores. The oracle computes the network on
+    # 24^3 neighbourhoods: with a receptive field of 4 voxels the central 16^3 of each block is
+    # exact although the block wraps periodically at its own edges.
+    C, torch = env
+    n = 128
+    net = make_net(C, n, seed=5, engine=1)
+    try:
+        psi = smooth_field(n, 9, 3.0)
+        d_psi = torch.from_numpy(psi).cuda()
+        out = torch.empty_like(d_psi)
+        C.colapm_nn_forward(net, d_psi, out)
+        got = grid(out.cpu().numpy(), n)
+        params = emulated(C.colapm_nn_get_params(net))
+        x = onn.bf16_round(grid(psi, n) / S_IN)
+        for cz, cy, cx in [(0, 0, 0), (70, 33, 101), (127, 64, 5)]:
+            iz, iy, ix = [(c + np.arange(-12, 12)) % n for c in (cz, cy, cx)]
+            ref, _ = onn.forward(x[np.ix_(iz, iy, ix)], params, store=onn.bf16_round)
+            ref = S_OUT * ref[4:20, 4:20, 4:20]
+            g = got[np.ix_(iz[4:20], iy[4:20], ix[4:20])]
+            rms = np.sqrt(np.mean(ref ** 2))
+            assert np.sqrt(np.mean((g - ref) ** 2)) < 2e-3 * rms
+            assert np.max(np.abs(g - ref)) < 2e-2 * rms
+    finally:
+        C.colapm_nn_destroy(net)
+
+
+def test_tcgen05_and_mma_sync_engines_agree(env):
+    C, torch = env
+    n = 128
+    tc = C.colapm_nn_create(n, C.nn_default_config(s_in=S_IN, s_out=S_OUT, seed=6, engine=1))
+    ms = C.colapm_nn_create(n, C.nn_default_config(s_in=S_IN, s_out=S_OUT, seed=6, engine=0))
+    try:
+        psi = torch.from_numpy(smooth_field(n, 10, 3.0)).cuda()
+        tgt = torch.from_numpy(smooth_field(n, 11, 0.4)).cuda()
+        oa, ob = torch.empty_like(psi), torch.empty_like(psi)
+        C.colapm_nn_forward(tc, psi, oa)
+        C.colapm_nn_forward(ms, psi, ob)
+        C.colapm_nn_sync(tc)
+        C.colapm_nn_sync(ms)
+        a, b = oa.double(), ob.double()
+        assert torch.sqrt(torch.mean((a - b) ** 2)).item() < 1e-3 * torch.sqrt(torch.mean(b ** 2)).item()
+        ga, la = C.colapm_nn_grads(tc, psi, tgt)
+        gb, lb = C.colapm_nn_grads(ms, psi, tgt)
+        assert abs(la / lb - 1) < 1e-4
+        for l, ((wa, ba), (wb, bb)) in enumerate(zip(onn.unflatten(ga.astype(np.float64)),
+                                                       onn.unflatten(gb.astype(np.float64)))):
+            assert np.linalg.norm(wa - wb) < 5e-3 * np.linalg.norm(wb), l
+            assert np.linalg.norm(ba - bb) < 5e-3 * np.linalg.norm(bb) + 1e-12, l
+    finally:
+        C.colapm_nn_destroy(tc)
+        C.colapm_nn_destroy(ms)
