@@ -22,6 +22,7 @@ struct colapm_ctx {
     // device buffers
     unsigned long long* rho = nullptr;   // nm^3 int64 fixed-point density
     float* F = nullptr;                  // 3 nm^3: density spectrum, then the three force meshes
+    float* Freal = nullptr;              // 3 nm^3: the real force meshes when the spectra use the blocked layout
     float4* pos = nullptr;               // np^3 (offsets, cell bits)
     float* mom = nullptr;                // 3 np^3, cells
     float* psi1 = nullptr;               // 3 np^3, cells
@@ -104,7 +105,7 @@ bool is_device_ptr(const void* p) {
 }
 
 void free_all(colapm_ctx* c) {
-    void* ptrs[] = {c->rho, c->F, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
+    void* ptrs[] = {c->rho, c->F, c->Freal, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
                     c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed, c->xy_ring, c->xy_ctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -151,6 +152,13 @@ int deposit(colapm_ctx* c) {
 
 bool use_xy(const colapm_ctx* c, int bit) { return (c->fused & bit) && c->xy_ring != nullptr; }
 
+// The two-stage engine keeps the half spectra in the blocked layout (see hs_index) unless the fused
+// x-y passes are selected; the inverse x pass then writes the real force meshes to Freal.
+bool use_blocked(const colapm_ctx* c) { return c->two_stage && !(c->fused & 3) && c->Freal != nullptr; }
+
+// The three real force meshes of the last force computation.
+const float* force_mesh(const colapm_ctx* c) { return use_blocked(c) ? c->Freal : c->F; }
+
 float density_scale(const colapm_ctx* c) {
     const double m = (double)c->nm / c->np;
     return (float)(m * m * m * std::ldexp(1.0, -45));
@@ -166,13 +174,14 @@ int density_xy(colapm_ctx* c) {
         c->rho_clean = true;
         return COLAPM_OK;
     }
-    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, c->two_stage, true));
+    const bool blk = use_blocked(c);
+    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, c->two_stage, true, blk));
     c->rho_clean = true;
-    CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream, c->two_stage));
+    CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream, c->two_stage, blk));
     return COLAPM_OK;
 }
 
-// §2.4 steps 1-3: the three real force meshes F_j = -d psi / dx_j (cells) in c->F.
+// §2.4 steps 1-3: the three real force meshes F_j = -d psi / dx_j (cells) in force_mesh(c).
 int compute_force(colapm_ctx* c) {
     int r = deposit(c);
     if (r) return r;
@@ -187,15 +196,18 @@ int compute_force(colapm_ctx* c) {
         out.p[1] = d + fs;
         out.p[2] = d + 2 * fs;
         const float gnorm = (float)(1.0 / ((double)c->nm * c->nm * c->nm));
-        CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream, c->two_stage));
+        CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream, c->two_stage,
+                      use_blocked(c)));
     }
     {
         Phase ph(c, COLAPM_PHASE_FFT_INV);
         if (use_xy(c, 2)) {
             CKL(launch_xy_inv(c->nm, d, fs, 3, c->tw_m, c->xy_ring, c->xy_ctr, c->err, c->stream));
         } else {
-            CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage));
-            CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage));
+            const bool blk = use_blocked(c);
+            CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk));
+            CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk,
+                              blk ? reinterpret_cast<float2*>(c->Freal) : nullptr));
         }
     }
     return COLAPM_OK;
@@ -303,6 +315,8 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
     if (ok && xy_supported(c->nm))
         ok = dalloc(reinterpret_cast<char**>(&c->xy_ring), xy_ring_bytes(c->nm)) == cudaSuccess &&
              dalloc(&c->xy_ctr, xy_ctr_ints(c->nm, 3)) == cudaSuccess;
+    // blocked spectra where every pass has a two-stage plan (the x passes need N/2 in 256, 512)
+    if (ok && (c->nm == 512 || c->nm == 1024)) ok = dalloc(&c->Freal, 3 * c->nm3) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -399,7 +413,7 @@ int colapm_step(colapm_ctx* c, int k) {
         int r = compute_force(c);
         if (r) return r;
         Phase ph(c, COLAPM_PHASE_GATHER);
-        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, coef_for(c, c->step), 1,
+        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, force_mesh(c), c->np3, c->nm, coef_for(c, c->step), 1,
                                     c->stream, c->block));
         ++c->step;
     }
@@ -421,7 +435,7 @@ int colapm_finalize(colapm_ctx* c) {
     }
     {
         Phase ph(c, COLAPM_PHASE_GATHER);
-        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, k, 0, c->stream, c->block));
+        CKL(launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, force_mesh(c), c->np3, c->nm, k, 0, c->stream, c->block));
     }
     if (c->prm.cola) CKL(launch_add_lpt_momentum(c->mom, c->psi1, c->psi2, c->np3, (float)g.p1, (float)g.p2, c->stream));
     c->finalized = true;
@@ -495,7 +509,7 @@ int power_enqueue(colapm_ctx* c, int nbins) {
     const double nm = c->nm;
     pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
     CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m, 0, 1.0f, &pw,
-                  c->stream, c->two_stage));
+                  c->stream, c->two_stage, use_blocked(c)));
     return COLAPM_OK;
 }
 
@@ -620,7 +634,7 @@ int colapm_get_force(colapm_ctx* c, float* force) {
     if (!c->has_ics) return COLAPM_E_STATE;
     int r = compute_force(c);
     if (r) return r;
-    copy_out(c, force, c->F, 3 * c->nm3 * sizeof(float));
+    copy_out(c, force, force_mesh(c), 3 * c->nm3 * sizeof(float));
     return pending_error(c);
 }
 
@@ -802,7 +816,7 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
                 r = compute_force(c);
                 if (r == COLAPM_OK && cudaGetLastError() == cudaSuccess) {
                     const int i = c->step < c->prm.n_steps ? c->step : c->prm.n_steps - 1;
-                    if (launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, c->F, c->np3, c->nm, coef_for(c, i), 1,
+                    if (launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, force_mesh(c), c->np3, c->nm, coef_for(c, i), 1,
                                                  c->stream, c->block) != cudaSuccess)
                         r = COLAPM_E_CUDA;
                 }

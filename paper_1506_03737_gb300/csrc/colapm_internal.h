@@ -64,16 +64,18 @@ __device__ __forceinline__ int power_bin(int n2, const int* lo, int nbins) {
 // `two_stage` selects the two-stage register FFT where it exists (256, 512, 1024 lines); the
 // shared-memory Stockham kernels otherwise.
 // zero_input: clear the int64 mesh as it is read, so that the next deposit needs no memset.
+// blocked: write the half spectrum in the blocked layout [kx/8][z][y][kx%8] (two-stage engine only).
 cudaError_t launch_fx_fwd_i64(int n_mesh, const unsigned long long* in, float2* out, const float2* tw,
-                              float scale, int* err, cudaStream_t s, bool two_stage = true, bool zero_input = false);
+                              float scale, int* err, cudaStream_t s, bool two_stage = true, bool zero_input = false,
+                              bool blocked = false);
 cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const float2* tw, cudaStream_t s,
                               bool two_stage = true);
 // Inverse x pass (c2r), in place, for `nfields` arrays spaced `field_stride` complex apart.
 cudaError_t launch_fx_inv(int n_mesh, float2* data, size_t field_stride, int nfields, const float2* tw,
-                          cudaStream_t s, bool two_stage = true);
+                          cudaStream_t s, bool two_stage = true, bool blocked = false, float2* dst = nullptr);
 // y pass in place (sign -1 forward, +1 inverse) on `nfields` arrays.
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
-                      cudaStream_t s, bool two_stage = true);
+                      cudaStream_t s, bool two_stage = true, bool blocked = false);
 // z pass with the spectral multiply fused.
 // Fused x-y passes (N = 512, 1024): forward r2c x + y of the int64 density into the half
 // spectrum `out`; inverse y + c2r x of `nfields` spectra in place. `ring` holds xy_ring_bytes(N)
@@ -87,7 +89,7 @@ cudaError_t launch_xy_inv(int nm, float2* data, size_t fstride, int nfields, con
                           int* err, cudaStream_t s);
 
 cudaError_t launch_fz(int n_mesh, int mode, float2* in, ZOut out, const float2* tw, const float* sinc2,
-                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage = true);
+                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage = true, bool blocked = false);
 
 // --- launchers (pm_kernels.cu) --------------------------------------------------------------
 cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s,

@@ -91,6 +91,16 @@ struct K2 {   // threads: the larger task count of the two stages (8 lines)
 
 __device__ __forceinline__ int sbin(int i, int L) { return i < L / 2 ? i : i - L; }
 
+// Half-spectrum layouts (n = L/2 complex columns kx, rows y, planes z): standard [z][y][kx], or
+// blocked [kx/8][z][y][kx%8]. In the blocked layout the 8-column tiles of the y pass are contiguous
+// and the rows of a z-pass tile are 64 KB apart instead of 4 MB (a 4 MB stride puts every row of a
+// tile in a different 2 MB page and streams at about a third of the bandwidth).
+template <int L, bool BLK>
+__device__ __forceinline__ size_t hs_index(int kx, int y, int z) {
+    if constexpr (BLK) return ((((size_t)(kx >> 3) * L + z) * L + y) << 3) + (kx & 7);
+    else return ((size_t)z * L + y) * (L / 2) + kx;
+}
+
 // Stage B of a line held in exchange buffer xb (stage-A radix RA), task j < RA of line c:
 // loads j + RA r, twiddles, RB-point DFT. Returns X[j + RA r] in v.
 template <int L, int RA, int RB, int S, int LINES = 8>
@@ -103,7 +113,7 @@ __device__ __forceinline__ void stage_b(const float2* xb, const Tw2* tw, int c, 
 
 // ---------------------------------------------------------------------------------------------
 // y pass (strided columns, stride n = L/2 complex), persistent over tiles of 8 columns.
-template <int L, int S>
+template <int L, int S, bool BLK = false>
 __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, size_t fstride,
                                                    const float2* __restrict__ tw, int nfields) {
     using K = K2<L>;
@@ -117,11 +127,12 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, siz
     const int tid = threadIdx.x, c = tid & 7, j = tid >> 3;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int f = t / TPF, r0 = t % TPF;
-        float2* g = data + (size_t)f * fstride + (size_t)(r0 / NG) * L * n + (r0 % NG) * 8 + c;
+        float2* g = data + (size_t)f * fstride + hs_index<L, BLK>((r0 % NG) * 8 + c, 0, r0 / NG);
+        constexpr size_t ys = BLK ? 8 : n;   // distance between rows y
         if (tid < K::TA) {
             float2 v[RA];
 #pragma unroll
-            for (int r = 0; r < RA; ++r) v[r] = __ldcg(g + (size_t)(j + r * (L / RA)) * n);
+            for (int r = 0; r < RA; ++r) v[r] = __ldcg(g + (size_t)(j + r * (L / RA)) * ys);
             dft<RA, S>(v);
 #pragma unroll
             for (int r = 0; r < RA; ++r) xb[Xch<L, RA>::at(c, j * RA + r)] = v[r];
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, siz
             float2 v[RB];
             stage_b<L, RA, RB, S>(xb, tws, c, j, v);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) g[(size_t)(j + RA * r) * n] = v[r];
+            for (int r = 0; r < RB; ++r) g[(size_t)(j + RA * r) * ys] = v[r];
         }
         __syncthreads();
     }
@@ -152,7 +163,7 @@ struct Z2 {
     static constexpr size_t SMEM = sizeof(float2) * ((size_t)XS * (1 + NSAVE) + PF) + sizeof(Tw2);
 };
 
-template <int L, int MODE, int C = 8>
+template <int L, int MODE, int C = 8, bool BLK = false>
 __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ in, ZOut out, const float2* __restrict__ tw,
                                                           const float* __restrict__ sinc2, int deconv, float gnorm,
                                                           PowerArgs pw) {
@@ -179,11 +190,12 @@ __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ 
     }
     __syncthreads();
     const float kf = 6.283185307179586f / (float)L;
-    const size_t stride = (size_t)L * n;
+    constexpr size_t stride = BLK ? (size_t)L * 8 : (size_t)L * n;   // distance between planes z
+    static_assert(!BLK || C == 8, "blocked layout needs 8-column tiles");
     const int tid = threadIdx.x, c = tid % C, j = tid / C;
     constexpr int TA = Z::TA, TB = Z::TB;   // forward stage-A / stage-B tasks
     auto prefetch = [&](int tt) {   // 16-byte cp.async.cg of rows z = 0..L-1, C columns, into pf
-        const size_t b = (size_t)(tt / NG) * n + (tt % NG) * C;
+        const size_t b = hs_index<L, BLK>((tt % NG) * C, tt / NG, 0);
         constexpr int Q = C / 2;    // 16-byte pieces per row
         for (int e = tid; e < L * Q; e += T) {
             const int z = e / Q, q = e % Q;
@@ -199,7 +211,7 @@ __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ 
         const int ky = t / NG, kx0 = (t % NG) * C;
         const int ny = sbin(ky, L);
         const bool nyq_y = (ky == L / 2);
-        const size_t base = (size_t)ky * n + kx0 + c;
+        const size_t base = hs_index<L, BLK>(kx0 + c, ky, 0);
         const int nx = kx0 + c;
         float2 v[R2];   // stage-B results: X[j + R1 r] (j < R1), or the LPT1 input spectrum
         if constexpr (MODE == Z_LPT1) {
@@ -371,7 +383,7 @@ struct X2 {
 
 // forward r2c: in = int64 density pairs (I64, converted to rho * scale - 1) or float reals.
 // zero (optional): the int64 input itself, cleared as it is read (the next deposit then needs no memset).
-template <int n, bool I64>
+template <int n, bool I64, bool BLK = false>
 __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ in_, float2* __restrict__ out,
                                                        const float2* __restrict__ tw, float scale, int* err,
                                                        int nitems, unsigned long long* zero) {
@@ -426,18 +438,18 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ i
         for (int e = tid; e < 8 * H; e += X::T) {
             const int c = e / H, k = e % H, k2 = (n - k) % n;
             const float2 a = xb[Xch<n, RA>::at(c, k)], b = xb[Xch<n, RA>::at(c, k2)];
-            float2* o = out + (row0 + c) * n;
+            const int y = (int)((row0 + c) % N), z = (int)((row0 + c) / N);
             {   // X[k] from Z[k] = a, Z[n-k] = b; w^k = exp(-2 pi i k / N) = tw[k]
                 const float2 bc = cconj(b);
                 const float2 E = cscale(cadd(a, bc), 0.5f);
                 const float2 d = csub(a, bc);
-                o[k] = cadd(E, cmul(tw[k], make_float2(0.5f * d.y, -0.5f * d.x)));
+                out[hs_index<N, BLK>(k, y, z)] = cadd(E, cmul(tw[k], make_float2(0.5f * d.y, -0.5f * d.x)));
             }
             if (k != 0 && k2 != k) {
                 const float2 ac = cconj(a);
                 const float2 E = cscale(cadd(b, ac), 0.5f);
                 const float2 d = csub(b, ac);
-                o[k2] = cadd(E, cmul(tw[k2], make_float2(0.5f * d.y, -0.5f * d.x)));
+                out[hs_index<N, BLK>(k2, y, z)] = cadd(E, cmul(tw[k2], make_float2(0.5f * d.y, -0.5f * d.x)));
             }
         }
         __syncthreads();
@@ -449,10 +461,12 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ i
 
 // inverse c2r in place on `nfields` arrays; the next tile's rows are prefetched into a dense
 // [8][n] staging buffer with 16-byte cp.async while the current one is transformed.
-template <int n>
+// With BLK the spectra are read in the blocked layout and the real rows written to `dst` (same field
+// stride), a separate array; otherwise dst == data and the pass is in place.
+template <int n, bool BLK = false>
 __global__ void __launch_bounds__(X2<n>::T) k2_fx_inv(float2* __restrict__ data, size_t fstride,
                                                        const float2* __restrict__ tw, int items_per_field,
-                                                       int nfields) {
+                                                       int nfields, float2* __restrict__ dst) {
     using X = X2<n>;
     constexpr int RA = X::RA, RB = X::RB, N = 2 * n, T = X::T;
     extern __shared__ float4 smem4[];
@@ -462,11 +476,20 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_inv(float2* __restrict__ data,
     load_tw2<n, N>(tws, tw, T);
     const int tid = threadIdx.x;
     const int nitems = items_per_field * nfields;
-    auto gptr = [&](int t) { return data + (size_t)(t / items_per_field) * fstride + (size_t)(t % items_per_field) * 8 * n; };
+    auto gptr = [&](int t) { return dst + (size_t)(t / items_per_field) * fstride + (size_t)(t % items_per_field) * 8 * n; };
     auto prefetch = [&](int t, int slot) {
-        const float2* g = gptr(t);
         float2* d = stg + slot * 8 * n;
-        for (int e = tid; e < 8 * n / 2; e += T) cp_async16_cg(d + 2 * e, g + 2 * e);
+        if constexpr (BLK) {   // 8 rows of one plane: per 8-column block, 8 rows x 64 B contiguous
+            const int row0 = (t % items_per_field) * 8, y0 = row0 % N, z = row0 / N;
+            const float2* g = data + (size_t)(t / items_per_field) * fstride;
+            for (int e = tid; e < 8 * n / 2; e += T) {
+                const int q = e & 3, c = (e >> 2) & 7, kxb = e >> 5;
+                cp_async16_cg(d + c * n + kxb * 8 + 2 * q, g + hs_index<N, true>(kxb * 8 + 2 * q, y0 + c, z));
+            }
+        } else {
+            const float2* g = data + (size_t)(t / items_per_field) * fstride + (size_t)(t % items_per_field) * 8 * n;
+            for (int e = tid; e < 8 * n / 2; e += T) cp_async16_cg(d + 2 * e, g + 2 * e);
+        }
         cp_async_commit();
     };
     if (blockIdx.x < nitems) prefetch(blockIdx.x, 0);

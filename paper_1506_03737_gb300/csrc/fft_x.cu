@@ -4,22 +4,30 @@
 
 namespace colapm {
 
+template <int n, bool I64, bool BLK>
+static cudaError_t fx_fwd2(const void* in, float2* out, const float2* tw, float scale, int* err, cudaStream_t s,
+                           unsigned long long* zero) {
+    using X = X2<n>;
+    static int grid2 = 0;
+    if (!grid2) {
+        cudaError_t e = set_smem(k2_fx_fwd<n, I64, BLK>, X::SMEM);
+        if (e != cudaSuccess) return e;
+        grid2 = persistent_grid(k2_fx_fwd<n, I64, BLK>, X::T, X::SMEM);
+    }
+    const int items = 2 * n * 2 * n / 8;
+    k2_fx_fwd<n, I64, BLK><<<grid2 < items ? grid2 : items, X::T, X::SMEM, s>>>(in, out, tw, scale, err, items, zero);
+    return cudaGetLastError();
+}
+
 template <int N, bool I64>
 static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float scale, int* err, cudaStream_t s,
-                            bool two_stage, unsigned long long* zero = nullptr) {
+                            bool two_stage, unsigned long long* zero = nullptr, bool blocked = false) {
     constexpr int n = N / 2;
     if constexpr (F2Has<n>::value) if (two_stage) {
-        using X = X2<n>;
-        static int grid2 = 0;
-        if (!grid2) {
-            cudaError_t e = set_smem(k2_fx_fwd<n, I64>, X::SMEM);
-            if (e != cudaSuccess) return e;
-            grid2 = persistent_grid(k2_fx_fwd<n, I64>, X::T, X::SMEM);
-        }
-        const int items = N * N / 8;
-        k2_fx_fwd<n, I64><<<grid2 < items ? grid2 : items, X::T, X::SMEM, s>>>(in, out, tw, scale, err, items, zero);
-        return cudaGetLastError();
+        return blocked ? fx_fwd2<n, I64, true>(in, out, tw, scale, err, s, zero)
+                       : fx_fwd2<n, I64, false>(in, out, tw, scale, err, s, zero);
     }
+    if (blocked) return cudaErrorInvalidValue;
     using C = FxFwd<n, I64>;
     static int grid = 0;
     if (!grid) {
@@ -32,22 +40,29 @@ static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float
     return cudaGetLastError();
 }
 
+template <int n, bool BLK>
+static cudaError_t fx_inv2(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s, float2* dst) {
+    using X = X2<n>;
+    static int grid2 = 0;
+    if (!grid2) {
+        cudaError_t e = set_smem(k2_fx_inv<n, BLK>, X::SMEM_INV);
+        if (e != cudaSuccess) return e;
+        grid2 = persistent_grid(k2_fx_inv<n, BLK>, X::T, X::SMEM_INV);
+    }
+    const int ipf = 2 * n * 2 * n / 8, items = ipf * nfields;
+    k2_fx_inv<n, BLK><<<grid2 < items ? grid2 : items, X::T, X::SMEM_INV, s>>>(data, fstride, tw, ipf, nfields, dst);
+    return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t fx_inv_t(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s,
-                            bool two_stage) {
+                            bool two_stage, bool blocked = false, float2* dst = nullptr) {
     constexpr int n = N / 2;
     if constexpr (F2Has<n>::value) if (two_stage) {
-        using X = X2<n>;
-        static int grid2 = 0;
-        if (!grid2) {
-            cudaError_t e = set_smem(k2_fx_inv<n>, X::SMEM_INV);
-            if (e != cudaSuccess) return e;
-            grid2 = persistent_grid(k2_fx_inv<n>, X::T, X::SMEM_INV);
-        }
-        const int ipf = N * N / 8, items = ipf * nfields;
-        k2_fx_inv<n><<<grid2 < items ? grid2 : items, X::T, X::SMEM_INV, s>>>(data, fstride, tw, ipf, nfields);
-        return cudaGetLastError();
+        if (blocked) return dst && dst != data ? fx_inv2<n, true>(data, fstride, nfields, tw, s, dst) : cudaErrorInvalidValue;
+        return fx_inv2<n, false>(data, fstride, nfields, tw, s, dst ? dst : data);
     }
+    if (blocked || (dst && dst != data)) return cudaErrorInvalidValue;
     using C = FxInv<n>;
     static int grid = 0;
     if (!grid) {
@@ -61,10 +76,10 @@ static cudaError_t fx_inv_t(float2* data, size_t fstride, int nfields, const flo
 }
 
 cudaError_t launch_fx_fwd_i64(int n_mesh, const unsigned long long* in, float2* out, const float2* tw,
-                              float scale, int* err, cudaStream_t s, bool two_stage, bool zero_input) {
+                              float scale, int* err, cudaStream_t s, bool two_stage, bool zero_input, bool blocked) {
     unsigned long long* z = zero_input ? const_cast<unsigned long long*>(in) : nullptr;
     switch (n_mesh) {
-#define X(N) case N: return fx_fwd_t<N, true>(in, out, tw, scale, err, s, two_stage, z);
+#define X(N) case N: return fx_fwd_t<N, true>(in, out, tw, scale, err, s, two_stage, z, blocked);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;
@@ -82,9 +97,9 @@ cudaError_t launch_fx_fwd_f32(int n_mesh, const float* in, float2* out, const fl
 }
 
 cudaError_t launch_fx_inv(int n_mesh, float2* data, size_t field_stride, int nfields, const float2* tw,
-                          cudaStream_t s, bool two_stage) {
+                          cudaStream_t s, bool two_stage, bool blocked, float2* dst) {
     switch (n_mesh) {
-#define X(N) case N: return fx_inv_t<N>(data, field_stride, nfields, tw, s, two_stage);
+#define X(N) case N: return fx_inv_t<N>(data, field_stride, nfields, tw, s, two_stage, blocked, dst);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;

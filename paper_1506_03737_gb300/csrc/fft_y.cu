@@ -4,22 +4,28 @@
 
 namespace colapm {
 
+template <int N, int S, bool BLK>
+static cudaError_t fy2(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
+    using K = K2<N>;
+    constexpr size_t smem = sizeof(float2) * Xch<N, K::RA>::SIZE + sizeof(Tw2);
+    static int grid2 = 0;
+    if (!grid2) {
+        cudaError_t e = set_smem(k2_fy<N, S, BLK>, smem);
+        if (e != cudaSuccess) return e;
+        grid2 = persistent_grid(k2_fy<N, S, BLK>, K::T, smem);
+    }
+    const int total = (N / 2 / 8) * N * nfields;
+    k2_fy<N, S, BLK><<<grid2 < total ? grid2 : total, K::T, smem, s>>>(data, fstride, tw, nfields);
+    return cudaGetLastError();
+}
+
 template <int N, int S>
 static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s,
-                           bool two_stage) {
+                           bool two_stage, bool blocked) {
     if constexpr (F2Has<N>::value) if (two_stage) {
-        using K = K2<N>;
-        constexpr size_t smem = sizeof(float2) * Xch<N, K::RA>::SIZE + sizeof(Tw2);
-        static int grid2 = 0;
-        if (!grid2) {
-            cudaError_t e = set_smem(k2_fy<N, S>, smem);
-            if (e != cudaSuccess) return e;
-            grid2 = persistent_grid(k2_fy<N, S>, K::T, smem);
-        }
-        const int total = (N / 2 / 8) * N * nfields;
-        k2_fy<N, S><<<grid2 < total ? grid2 : total, K::T, smem, s>>>(data, fstride, tw, nfields);
-        return cudaGetLastError();
+        return blocked ? fy2<N, S, true>(data, fstride, nfields, tw, s) : fy2<N, S, false>(data, fstride, nfields, tw, s);
     }
+    if (blocked) return cudaErrorInvalidValue;
     using C = Fy<N>;
     constexpr size_t smem = C::SMEM;
     static int grid = 0;
@@ -35,15 +41,15 @@ static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const floa
 
 template <int N>
 static cudaError_t fy_t(int sign, float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s,
-                        bool two_stage) {
-    return sign < 0 ? fy_sign<N, -1>(data, fstride, nfields, tw, s, two_stage)
-                    : fy_sign<N, +1>(data, fstride, nfields, tw, s, two_stage);
+                        bool two_stage, bool blocked) {
+    return sign < 0 ? fy_sign<N, -1>(data, fstride, nfields, tw, s, two_stage, blocked)
+                    : fy_sign<N, +1>(data, fstride, nfields, tw, s, two_stage, blocked);
 }
 
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
-                      cudaStream_t s, bool two_stage) {
+                      cudaStream_t s, bool two_stage, bool blocked) {
     switch (n_mesh) {
-#define X(N) case N: return fy_t<N>(sign, data, field_stride, nfields, tw, s, two_stage);
+#define X(N) case N: return fy_t<N>(sign, data, field_stride, nfields, tw, s, two_stage, blocked);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;

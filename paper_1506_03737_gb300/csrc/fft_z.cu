@@ -4,25 +4,37 @@
 
 namespace colapm {
 
+template <int N, int MODE, bool BLK>
+static cudaError_t fz2(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm, PowerArgs pw,
+                       cudaStream_t s) {
+    constexpr int CZ = 8;   // 4-column tiles fit two CTAs per SM but measured slower (32-byte rows)
+    using Z = Z2<N, MODE, CZ>;
+    const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
+    static size_t configured2 = 0;
+    static int grid2 = 0;
+    if (smem > configured2 || !grid2) {
+        cudaError_t e = set_smem(k2_fz<N, MODE, CZ, BLK>, smem);
+        if (e != cudaSuccess) return e;
+        configured2 = smem > configured2 ? smem : configured2;
+        grid2 = persistent_grid(k2_fz<N, MODE, CZ, BLK>, Z::T, smem);
+    }
+    const int total = (N / 2 / CZ) * N;
+    k2_fz<N, MODE, CZ, BLK><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
+    return cudaGetLastError();
+}
+
 template <int N, int MODE>
 static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm,
-                           PowerArgs pw, cudaStream_t s, bool two_stage) {
+                           PowerArgs pw, cudaStream_t s, bool two_stage, bool blocked) {
     if constexpr (F2Has<N>::value) if (two_stage) {
-        constexpr int CZ = 8;   // 4-column tiles fit two CTAs per SM but measured slower (32-byte rows)
-        using Z = Z2<N, MODE, CZ>;
-        const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
-        static size_t configured2 = 0;
-        static int grid2 = 0;
-        if (smem > configured2 || !grid2) {
-            cudaError_t e = set_smem(k2_fz<N, MODE, CZ>, smem);
-            if (e != cudaSuccess) return e;
-            configured2 = smem > configured2 ? smem : configured2;
-            grid2 = persistent_grid(k2_fz<N, MODE, CZ>, Z::T, smem);
+        if constexpr (MODE == Z_FORCE || MODE == Z_POWER) {
+            if (blocked) return fz2<N, MODE, true>(in, out, tw, sinc2, deconv, gnorm, pw, s);
+        } else {
+            if (blocked) return cudaErrorInvalidValue;
         }
-        const int total = (N / 2 / CZ) * N;
-        k2_fz<N, MODE, CZ><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
-        return cudaGetLastError();
+        return fz2<N, MODE, false>(in, out, tw, sinc2, deconv, gnorm, pw, s);
     }
+    if (blocked) return cudaErrorInvalidValue;
     using C = Fz<N, MODE>;
     const size_t smem = C::BASE_SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
     static size_t configured = 0;
@@ -40,22 +52,22 @@ static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* 
 
 template <int N>
 static cudaError_t fz_t(int mode, float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv,
-                        float gnorm, const PowerArgs* pwp, cudaStream_t s, bool ts) {
+                        float gnorm, const PowerArgs* pwp, cudaStream_t s, bool ts, bool blk) {
     PowerArgs pw{};
     if (pwp) pw = *pwp;
     switch (mode) {
-        case Z_FORCE: return fz_mode<N, Z_FORCE>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
-        case Z_LPT1: return fz_mode<N, Z_LPT1>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
-        case Z_LPT2: return fz_mode<N, Z_LPT2>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
-        case Z_POWER: return fz_mode<N, Z_POWER>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts);
+        case Z_FORCE: return fz_mode<N, Z_FORCE>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts, blk);
+        case Z_LPT1: return fz_mode<N, Z_LPT1>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts, blk);
+        case Z_LPT2: return fz_mode<N, Z_LPT2>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts, blk);
+        case Z_POWER: return fz_mode<N, Z_POWER>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts, blk);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_fz(int n_mesh, int mode, float2* in, ZOut out, const float2* tw, const float* sinc2,
-                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage) {
+                      int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage, bool blocked) {
     switch (n_mesh) {
-#define X(N) case N: return fz_t<N>(mode, in, out, tw, sinc2, deconv, gnorm, pw, s, two_stage);
+#define X(N) case N: return fz_t<N>(mode, in, out, tw, sinc2, deconv, gnorm, pw, s, two_stage, blocked);
         COLAPM_FOR_MESH_SIZES(X)
 #undef X
         default: return cudaErrorInvalidValue;
