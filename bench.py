@@ -376,8 +376,8 @@ def main():
         nbytes += 12 * nm ** 3
     achieved = nbytes / (per_call[dom] / 1e3) / 1e9
     # DRAM bytes (read + write) per cell of the force z pass from an ncu capture of the same
-    # kernel at 512^3 (537.0 MB + 1556.3 MB), scaled by the cell count; none for the gather.
-    traffic = 2093.3e6 / 512 ** 3 * nm ** 3 if dom == "poisson" else None
+    # kernel at 512^3 (583.9 MB + 1564.4 MB), scaled by the cell count; none for the gather.
+    traffic = 2148.3e6 / 512 ** 3 * nm ** 3 if dom == "poisson" else None
     alg_step = ALG_BYTES_PARTICLE * np_ ** 3 + ALG_BYTES_CELL * nm ** 3
 
     line = {
