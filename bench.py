@@ -33,8 +33,8 @@ ALG_BYTES_PARTICLE = 96
 ALG_BYTES_CELL = 80
 # Per-kernel algorithmic bytes per cell (mesh kernels) or particle (particle kernels).
 ALG_PHASE = {
-    "poisson": ("cell", 16),     # z pass: read the half spectrum once, write three force spectra
-    "fft_inv": ("cell", 24),     # inverse passes: read three spectra, write three real meshes
+    "poisson": ("cell", 12),     # z pass: read the half spectrum, write the two inverse-z bases
+    "fft_inv": ("cell", 44),     # inverse y (2 bases -> 3 spectra, 20 B) + inverse x (3 fields, 24 B)
     "fft_fwd": ("cell", 12),     # forward passes: read int64 density, write half spectrum
     "deposit": ("cell", 16),     # zero + atomic write-back of the int64 mesh (+16 B/particle below)
     "gather": ("particle", 80),  # read pos, mom, psi1, psi2, write pos, mom (+12 B/cell below)
@@ -375,9 +375,9 @@ def main():
     if dom == "gather":
         nbytes += 12 * nm ** 3
     achieved = nbytes / (per_call[dom] / 1e3) / 1e9
-    # DRAM bytes (read + write) per cell of the force z pass from an ncu capture of the same
-    # kernel at 512^3 (583.9 MB + 1564.4 MB), scaled by the cell count; none for the gather.
-    traffic = 2148.3e6 / 512 ** 3 * nm ** 3 if dom == "poisson" else None
+    # DRAM bytes per launch of the dominant kernel from an ncu capture of the same kernel (none yet
+    # for the current force z pass, which writes two bases instead of three spectra).
+    traffic = None
     alg_step = ALG_BYTES_PARTICLE * np_ ** 3 + ALG_BYTES_CELL * nm ** 3
 
     line = {

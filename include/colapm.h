@@ -204,8 +204,7 @@ int colapm_autotune(colapm_ctx* ctx, int* choice);
 /* Select the configuration explicitly (e.g. to compare engines or to pin a choice): fused x-y
  * passes as a bit mask (1 forward, 2 inverse, 3 both; default 0; ignored where N_m has none),
  * two-stage register FFT (else Stockham) and the particle-kernel block size (128, 256 or 512);
- * COLAPM_E_ARG otherwise. All engines compute the same transforms; fused and two-stage passes
- * give bit-identical results. */
+ * COLAPM_E_ARG otherwise. All engines compute the same transforms and agree to FP32 rounding. */
 int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
 
 /* ---- batched mocks (many independent realisations of uneven sizes) ----------------------- */

@@ -205,7 +205,11 @@ int compute_force(colapm_ctx* c) {
             CKL(launch_xy_inv(c->nm, d, fs, 3, c->tw_m, c->xy_ring, c->xy_ctr, c->err, c->stream));
         } else {
             const bool blk = use_blocked(c);
-            CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk));
+            if (blk) {
+                CKL(launch_fy_force(c->nm, d, fs, c->tw_m, c->stream));   // bases -> three spectra
+            } else {
+                CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk));
+            }
             CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk,
                               blk ? reinterpret_cast<float2*>(c->Freal) : nullptr));
         }

@@ -76,6 +76,10 @@ cudaError_t launch_fx_inv(int n_mesh, float2* data, size_t field_stride, int nfi
 // y pass in place (sign -1 forward, +1 inverse) on `nfields` arrays.
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
                       cudaStream_t s, bool two_stage = true, bool blocked = false);
+// Inverse y pass of the force in the blocked layout (N = 512, 1024): from the z pass's two bases in
+// fields 0 and 2 to the three force spectra in fields 0, 1, 2 (the blocked force z pass writes
+// the bases instead of the three spectra).
+cudaError_t launch_fy_force(int n_mesh, float2* data, size_t field_stride, const float2* tw, cudaStream_t s);
 // z pass with the spectral multiply fused.
 // Fused x-y passes (N = 512, 1024): forward r2c x + y of the int64 density into the half
 // spectrum `out`; inverse y + c2r x of `nfields` spectra in place. `ring` holds xy_ring_bytes(N)

@@ -335,7 +335,9 @@ __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ 
                         const size_t o = base + (size_t)(j + R2 * r) * stride;
                         const float2 a = u[r];
                         const float2 ia = make_float2(-a.y, a.x);   // i * a
-                        if (bi == 0) {
+                        if (MODE == Z_FORCE && BLK) {   // bases only; k2_fy_force applies i k_x, i k_y, i
+                            out.p[bi == 0 ? 0 : 2][o] = a;
+                        } else if (bi == 0) {
                             out.p[0][o] = cscale(ia, sg * kxv);
                             out.p[1][o] = cscale(ia, sg * kyv);
                             if constexpr (MODE == Z_LPT1) {
@@ -366,6 +368,60 @@ __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ 
                 atomicAdd(&pw.ksum[b], ksum[b]);
                 atomicAdd(&pw.cnt[b], cnt[b]);
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Inverse y pass of the force in the blocked layout. The z pass leaves the two inverse-z bases
+// A' = IFFT_z(g X) in field 0 and B' = IFFT_z(k_z g X) in field 2 (k_x and k_y are constant along
+// a z line, so the three force spectra are i k_x A', i k_y A' and i B'). Per 8-column tile this
+// kernel makes the three y transforms from the two inputs:
+//   F_z = i IFFT_y(B')         -> field 2 (in place)
+//   F_y = i IFFT_y(k_y A')     -> field 1
+//   F_x = i k_x IFFT_y(A')     -> field 0 (in place; A' is read twice, the second time from L2)
+// It reads 8 bytes per cell instead of the 12 of three separate spectra.
+template <int L>
+__global__ void __launch_bounds__(K2<L>::T) k2_fy_force(float2* __restrict__ data, size_t fstride,
+                                                        const float2* __restrict__ tw) {
+    using K = K2<L>;
+    constexpr int RA = K::RA, RB = K::RB, n = L / 2, NG = n / 8, TPF = NG * L;
+    extern __shared__ float4 smem4[];
+    float2* xb = reinterpret_cast<float2*>(smem4);
+    Tw2* tws = reinterpret_cast<Tw2*>(xb + Xch<L, RA>::SIZE);
+    load_tw2<L, L>(tws, tw, K::T);
+    __syncthreads();
+    const float kf = 6.283185307179586f / (float)L;
+    const int tid = threadIdx.x, c = tid & 7, j = tid >> 3;
+    for (int t = blockIdx.x; t < TPF; t += gridDim.x) {
+        const int kx = (t % NG) * 8 + c;
+        const size_t off = hs_index<L, true>(kx, 0, t / NG);   // rows y are 8 complex apart
+        const float kxv = kf * (float)kx;
+#pragma unroll 1
+        for (int pass = 0; pass < 3; ++pass) {
+            const float2* src = data + (pass == 0 ? 2 * fstride : 0) + off;
+            float2* dst = data + (pass == 0 ? 2 : (pass == 1 ? 1 : 0)) * fstride + off;
+            if (tid < K::TA) {
+                float2 v[RA];
+#pragma unroll
+                for (int r = 0; r < RA; ++r) {
+                    const int y = j + r * (L / RA);
+                    v[r] = __ldcg(src + (size_t)y * 8);
+                    if (pass == 1) v[r] = cscale(v[r], kf * (float)sbin(y, L));
+                }
+                dft<RA, +1>(v);
+#pragma unroll
+                for (int r = 0; r < RA; ++r) xb[Xch<L, RA>::at(c, j * RA + r)] = v[r];
+            }
+            __syncthreads();
+            if (tid < K::TB) {
+                float2 u[RB];
+                stage_b<L, RA, RB, +1>(xb, tws, c, j, u);
+                const float sc = pass == 2 ? kxv : 1.0f;
+#pragma unroll
+                for (int r = 0; r < RB; ++r) dst[(size_t)(j + RA * r) * 8] = make_float2(-sc * u[r].y, sc * u[r].x);
+            }
+            __syncthreads();
         }
     }
 }

@@ -46,6 +46,29 @@ static cudaError_t fy_t(int sign, float2* data, size_t fstride, int nfields, con
                     : fy_sign<N, +1>(data, fstride, nfields, tw, s, two_stage, blocked);
 }
 
+template <int N>
+static cudaError_t fy_force_t(float2* data, size_t fstride, const float2* tw, cudaStream_t s) {
+    using K = K2<N>;
+    constexpr size_t smem = sizeof(float2) * Xch<N, K::RA>::SIZE + sizeof(Tw2);
+    static int grid = 0;
+    if (!grid) {
+        cudaError_t e = set_smem(k2_fy_force<N>, smem);
+        if (e != cudaSuccess) return e;
+        grid = persistent_grid(k2_fy_force<N>, K::T, smem);
+    }
+    const int total = (N / 2 / 8) * N;
+    k2_fy_force<N><<<grid < total ? grid : total, K::T, smem, s>>>(data, fstride, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fy_force(int n_mesh, float2* data, size_t field_stride, const float2* tw, cudaStream_t s) {
+    switch (n_mesh) {
+        case 512: return fy_force_t<512>(data, field_stride, tw, s);
+        case 1024: return fy_force_t<1024>(data, field_stride, tw, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_fy(int n_mesh, int sign, float2* data, size_t field_stride, int nfields, const float2* tw,
                       cudaStream_t s, bool two_stage, bool blocked) {
     switch (n_mesh) {

@@ -3,8 +3,8 @@
 - Planar slabs: particles sit on cell nodes filling whole x-, y- and z-planes (exactly N_p^3 of
   them), so the density is an exact integer pattern that varies along one axis per slab set. The
   force is then exactly the sum of three 1-D solutions (oracle planar_force_1d), at any mesh size.
-- Engines: on a clustered state the fused x-y passes give bit-identical force meshes to the
-  separate two-stage passes, and the Stockham engine agrees to FP32 rounding.
+- Engines: on a clustered state the default two-stage passes (blocked layout, two-base force
+  form), the fused x-y passes and the Stockham engine agree to FP32 rounding.
 - 256^3: the oracle's full 3-D force (numpy FFT primitive) on a clustered state.
 """
 import numpy as np
@@ -89,9 +89,11 @@ def test_engines_agree_at_1024(env):
             f = torch.empty(3 * nm ** 3, dtype=torch.float32, device="cuda")
             C.colapm_get_force(ctx, f)
             out[name] = f
-        assert torch.equal(out["fused"], out["two_stage"])
-        a, b = out["fused"].double(), out["stockham"].double()
-        assert torch.sqrt(torch.mean((a - b) ** 2)).item() < 1e-5 * torch.sqrt(torch.mean(b ** 2)).item()
+        ref = out["two_stage"].double()
+        scale = torch.sqrt(torch.mean(ref ** 2)).item()
+        for name in ("fused", "stockham"):
+            diff = out[name].double() - ref
+            assert torch.sqrt(torch.mean(diff ** 2)).item() < 1e-5 * scale, name
     finally:
         C.colapm_destroy(ctx)
 
