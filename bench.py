@@ -375,9 +375,9 @@ def main():
     if dom == "gather":
         nbytes += 12 * nm ** 3
     achieved = nbytes / (per_call[dom] / 1e3) / 1e9
-    # DRAM bytes per launch of the dominant kernel from an ncu capture of the same kernel (none yet
-    # for the current force z pass, which writes two bases instead of three spectra).
-    traffic = None
+    # DRAM bytes (read + write) per cell of the force z pass from an ncu capture of the same
+    # kernel at 512^3 (548.2 MB + 1021.5 MB), scaled by the cell count; none for the gather.
+    traffic = 1569.7e6 / 512 ** 3 * nm ** 3 if dom == "poisson" else None
     alg_step = ALG_BYTES_PARTICLE * np_ ** 3 + ALG_BYTES_CELL * nm ** 3
 
     line = {
