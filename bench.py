@@ -62,6 +62,28 @@ def dist_env():
     return rank, world, local
 
 
+def mock_seed(rank, phase, i):
+    """Seed of the i-th mock a rank draws in a phase (0 warm-up, 1 timed, 2 end to end, 3 batch
+    setup, 4 + r batch replay r): disjoint across ranks and phases for i < 10^5."""
+    return 10 ** 7 * (rank + 1) + 10 ** 5 * phase + i
+
+
+def reduce_max(x, dist):
+    """Maximum of x over the ranks of the default process group (x itself on one rank)."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -183,24 +205,25 @@ def batch_params(C, base_seed=1000):
     return out
 
 
-def run_batch(C, stream, rank, args):
-    """Mocks/hour of the 64-mock uneven batch: one CUDA graph per batch, replayed with new seeds."""
+def run_batch(C, stream, rank, args, world=1, dist=None):
+    """Mocks/hour of the 64-mock uneven batch: one CUDA graph per batch, replayed with new seeds;
+    with several ranks each replays its own batch and the figures are for the whole job."""
     params = batch_params(C)
     ups = sum(p.np ** 3 * p.n_steps for p in params)
     b = C.colapm_batch_create(params, nstreams=0, stream=stream.cuda_stream)
     try:
         t0 = time.perf_counter()
-        C.colapm_batch_run(b, 64, 100, seeds=[7000 + 64 * rank + i for i in range(64)])   # capture + stream choice
+        C.colapm_batch_run(b, 64, 100, seeds=[mock_seed(rank, 3, i) for i in range(64)])   # capture + stream choice
         setup = time.perf_counter() - t0
         reps = 2
         t0 = time.perf_counter()
         for rep in range(reps):
-            C.colapm_batch_run(b, 64, 100, seeds=[9000 + 1000 * rep + 64 * rank + i for i in range(64)])
-        secs = (time.perf_counter() - t0) / reps
+            C.colapm_batch_run(b, 64, 100, seeds=[mock_seed(rank, 4 + rep, i) for i in range(64)])
+        secs = reduce_max((time.perf_counter() - t0) / reps, dist)
         return {"workload": "64 mocks, N_p = 64..192 (step 32), N_m = 2 N_p, L = 128..512 Mpc/h, 10 COLA steps, "
                             "2LPT ICs + 100-bin P(k) each; one CUDA graph, new seeds per replay",
-                "mocks_per_hour": 64 * 3600.0 / secs, "ms_per_batch": 1e3 * secs,
-                "particle_updates_per_s": ups / secs, "worker_streams": C.colapm_batch_streams(b),
+                "mocks_per_hour": 64 * world * 3600.0 / secs, "ms_per_batch": 1e3 * secs,
+                "particle_updates_per_s": ups * world / secs, "worker_streams": C.colapm_batch_streams(b),
                 "first_run_s_incl_capture_and_tuning": setup}
     finally:
         C.colapm_batch_destroy(b)
@@ -294,11 +317,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist)
 
     kw = workloads.run_params(args.workload)
     np_, nm, nsteps = kw["np"], kw["nm"], kw["n_steps"]
@@ -315,9 +334,8 @@ def main():
         C.colapm_step(ctx, -1)
         C.colapm_power(ctx, nbins, 0.0, 0.0, k_out, p_out, n_out)
 
-    seed0 = 1000 * (rank + 1)
     for w in range(args.warmup):
-        mock(seed0 + w, kd, pd, nd)
+        mock(mock_seed(rank, 0, w), kd, pd, nd)
     C.colapm_get_timing(ctx)                     # clear
     C.colapm_set_timing(ctx, True)
     launches0 = C.colapm_kernel_launches(ctx)
@@ -327,7 +345,7 @@ def main():
     with Clocks(local) as clk:
         ev0.record(stream)
         for s in range(args.steps):
-            mock(seed0 + 100 + s, kd, pd, nd)
+            mock(mock_seed(rank, 1, s), kd, pd, nd)
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -338,7 +356,7 @@ def main():
     C.colapm_set_timing(ctx, False)
 
     updates = np_ ** 3 * nsteps * args.steps * world
-    value = updates / (ms_max / 1e3)
+    value = job_value(np_ ** 3 * nsteps * args.steps, world, ms_max)
 
     # end to end: host buffers through the public C calls, the step's result read back to host
     e2e = None
@@ -351,7 +369,7 @@ def main():
         barrier()
         t0 = time.perf_counter()
         for s in range(args.steps):
-            mock(seed0 + 200 + s, kh, ph, nh)
+            mock(mock_seed(rank, 2, s), kh, ph, nh)
             C.colapm_get_particles(ctx, posh, momh)
         torch.cuda.synchronize()
         barrier()
@@ -404,8 +422,8 @@ def main():
         line["e2e"] = e2e
     C.colapm_destroy(ctx)
     if not args.no_batch:
-        line["batch"] = run_batch(C, stream, rank, args)
-    if not args.no_learned:
+        line["batch"] = run_batch(C, stream, rank, args, world, dist)
+    if not args.no_learned and rank == 0:   # one training run; the other ranks have nothing to add
         line["learned"] = run_learned(C, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
