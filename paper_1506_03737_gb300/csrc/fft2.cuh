@@ -92,13 +92,24 @@ struct K2 {   // threads: the larger task count of the two stages (8 lines)
 __device__ __forceinline__ int sbin(int i, int L) { return i < L / 2 ? i : i - L; }
 
 // Half-spectrum layouts (n = L/2 complex columns kx, rows y, planes z): standard [z][y][kx], or
-// blocked [kx/8][z][y][kx%8]. In the blocked layout the 8-column tiles of the y pass are contiguous
-// and the rows of a z-pass tile are 64 KB apart instead of 4 MB (a 4 MB stride puts every row of a
-// tile in a different 2 MB page and streams at about a third of the bandwidth).
+// blocked [kx/8][y/8][z][y%8][kx%8]. In the blocked layout every tile the passes read is made of
+// 512-byte runs: an x-pass tile of 8 rows is one run per 8-column block, a y-pass tile takes one
+// run per group of 8 rows, and the rows of a z-pass tile are 512 bytes apart (64 bytes each; the
+// 8 tiles of one row group, taken one after the other, complete every run). In the standard layout
+// the rows of a z tile are 4 MB apart, every one in a different 2 MB page, which streams at about a
+// third of the bandwidth.
 template <int L, bool BLK>
 __device__ __forceinline__ size_t hs_index(int kx, int y, int z) {
-    if constexpr (BLK) return ((((size_t)(kx >> 3) * L + z) * L + y) << 3) + (kx & 7);
+    if constexpr (BLK)
+        return ((((((size_t)(kx >> 3) * (L / 8) + (y >> 3)) * L + z) << 3) + (y & 7)) << 3) + (kx & 7);
     else return ((size_t)z * L + y) * (L / 2) + kx;
+}
+
+// Distance between rows y and y + d of one column when d and y are multiples of 8 apart from the
+// same residue (d a multiple of 8): what the passes add per register index.
+template <int L, bool BLK>
+__device__ __forceinline__ constexpr size_t hs_ystep(int d) {
+    return BLK ? (size_t)(d / 8) * L * 64 : (size_t)d * (L / 2);
 }
 
 // Stage B of a line held in exchange buffer xb (stage-A radix RA), task j < RA of line c:
@@ -127,12 +138,12 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, siz
     const int tid = threadIdx.x, c = tid & 7, j = tid >> 3;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int f = t / TPF, r0 = t % TPF;
-        float2* g = data + (size_t)f * fstride + hs_index<L, BLK>((r0 % NG) * 8 + c, 0, r0 / NG);
-        constexpr size_t ys = BLK ? 8 : n;   // distance between rows y
+        // rows y = j + r L/RA (stage A) and j + RA r (stage B); L/RA and RA are multiples of 8
+        float2* g = data + (size_t)f * fstride + hs_index<L, BLK>((r0 % NG) * 8 + c, j, r0 / NG);
         if (tid < K::TA) {
             float2 v[RA];
 #pragma unroll
-            for (int r = 0; r < RA; ++r) v[r] = __ldcg(g + (size_t)(j + r * (L / RA)) * ys);
+            for (int r = 0; r < RA; ++r) v[r] = __ldcg(g + r * hs_ystep<L, BLK>(L / RA));
             dft<RA, S>(v);
 #pragma unroll
             for (int r = 0; r < RA; ++r) xb[Xch<L, RA>::at(c, j * RA + r)] = v[r];
@@ -142,7 +153,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, siz
             float2 v[RB];
             stage_b<L, RA, RB, S>(xb, tws, c, j, v);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) g[(size_t)(j + RA * r) * ys] = v[r];
+            for (int r = 0; r < RB; ++r) g[r * hs_ystep<L, BLK>(RA)] = v[r];
         }
         __syncthreads();
     }
@@ -190,12 +201,27 @@ __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ 
     }
     __syncthreads();
     const float kf = 6.283185307179586f / (float)L;
-    constexpr size_t stride = BLK ? (size_t)L * 8 : (size_t)L * n;   // distance between planes z
-    static_assert(!BLK || C == 8, "blocked layout needs 8-column tiles");
+    constexpr size_t stride = BLK ? (size_t)64 : (size_t)L * n;   // distance between planes z
+    // tile -> (ky, kx0); in the blocked layout the 8 ky of a row group, then the 8 / C column
+    // sub-tiles of an 8-column block, are consecutive tiles (together they cover 512-byte runs)
+    auto tile_of = [&](int tt, int& ky_, int& kx0_) {
+        if constexpr (BLK) {
+            constexpr int SUB = 8 / C;
+            const int q = tt >> 3;
+            ky_ = 8 * (q / (SUB * (n / 8))) + (tt & 7);
+            kx0_ = ((q / SUB) % (n / 8)) * 8 + (q % SUB) * C;
+        } else {
+            ky_ = tt / NG;
+            kx0_ = (tt % NG) * C;
+        }
+    };
+    static_assert(!BLK || C == 8 || C == 4, "blocked layout needs 8- or 4-column tiles");
     const int tid = threadIdx.x, c = tid % C, j = tid / C;
     constexpr int TA = Z::TA, TB = Z::TB;   // forward stage-A / stage-B tasks
     auto prefetch = [&](int tt) {   // 16-byte cp.async.cg of rows z = 0..L-1, C columns, into pf
-        const size_t b = hs_index<L, BLK>((tt % NG) * C, tt / NG, 0);
+        int pky, pkx0;
+        tile_of(tt, pky, pkx0);
+        const size_t b = hs_index<L, BLK>(pkx0, pky, 0);
         constexpr int Q = C / 2;    // 16-byte pieces per row
         for (int e = tid; e < L * Q; e += T) {
             const int z = e / Q, q = e % Q;
@@ -208,7 +234,8 @@ __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ 
     }
 
     for (int t = blockIdx.x; t < NTILE; t += gridDim.x) {
-        const int ky = t / NG, kx0 = (t % NG) * C;
+        int ky, kx0;
+        tile_of(t, ky, kx0);
         const int ny = sbin(ky, L);
         const bool nyq_y = (ky == L / 2);
         const size_t base = hs_index<L, BLK>(kx0 + c, ky, 0);
@@ -395,7 +422,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy_force(float2* __restrict__ dat
     const int tid = threadIdx.x, c = tid & 7, j = tid >> 3;
     for (int t = blockIdx.x; t < TPF; t += gridDim.x) {
         const int kx = (t % NG) * 8 + c;
-        const size_t off = hs_index<L, true>(kx, 0, t / NG);   // rows y are 8 complex apart
+        const size_t off = hs_index<L, true>(kx, j, t / NG);   // row j; other rows at hs_ystep offsets
         const float kxv = kf * (float)kx;
 #pragma unroll 1
         for (int pass = 0; pass < 3; ++pass) {
@@ -406,7 +433,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy_force(float2* __restrict__ dat
 #pragma unroll
                 for (int r = 0; r < RA; ++r) {
                     const int y = j + r * (L / RA);
-                    v[r] = __ldcg(src + (size_t)y * 8);
+                    v[r] = __ldcg(src + r * hs_ystep<L, true>(L / RA));
                     if (pass == 1) v[r] = cscale(v[r], kf * (float)sbin(y, L));
                 }
                 dft<RA, +1>(v);
@@ -419,7 +446,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy_force(float2* __restrict__ dat
                 stage_b<L, RA, RB, +1>(xb, tws, c, j, u);
                 const float sc = pass == 2 ? kxv : 1.0f;
 #pragma unroll
-                for (int r = 0; r < RB; ++r) dst[(size_t)(j + RA * r) * 8] = make_float2(-sc * u[r].y, sc * u[r].x);
+                for (int r = 0; r < RB; ++r) dst[r * hs_ystep<L, true>(RA)] = make_float2(-sc * u[r].y, sc * u[r].x);
             }
             __syncthreads();
         }

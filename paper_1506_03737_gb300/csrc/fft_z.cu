@@ -7,7 +7,10 @@ namespace colapm {
 template <int N, int MODE, bool BLK>
 static cudaError_t fz2(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm, PowerArgs pw,
                        cudaStream_t s) {
-    constexpr int CZ = 8;   // 4-column tiles fit two CTAs per SM but measured slower (32-byte rows)
+    // Blocked layout: 4-column tiles (two CTAs per SM; 32-byte rows whose 512-byte runs the
+    // neighbouring tiles complete) measured 2% faster than 8-column ones, and 34% faster for the
+    // power spectrum. Standard layout: 8 columns (4-column rows there are 32 bytes 4 MB apart).
+    constexpr int CZ = BLK ? 4 : 8;
     using Z = Z2<N, MODE, CZ>;
     const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
     static size_t configured2 = 0;
