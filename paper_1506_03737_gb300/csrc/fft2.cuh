@@ -163,22 +163,26 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, siz
 // z pass with the spectral operator fused (see k_fz in fft_kernels.cuh for the algebra):
 // forward z (radices R1, R2) -> bases in registers -> inverse z (radices R2, R1) per base.
 // C columns per tile (8, or 4 to halve shared memory and fit two CTAs per SM).
-template <int L, int MODE, int C = 8>
+template <int L, int MODE, int C = 8, bool DIRECT = false>
 struct Z2 {
     static constexpr int R1 = F2<L>::R1, R2 = F2<L>::R2;
     static constexpr int XS = Xch<L, R1, C>::SIZE > Xch<L, R2, C>::SIZE ? Xch<L, R1, C>::SIZE : Xch<L, R2, C>::SIZE;
     static constexpr int NSAVE = MODE == Z_LPT1 ? 2 : (MODE == Z_POWER ? 0 : 1);   // saved bases B (, C)
-    static constexpr bool PREFETCH = MODE != Z_LPT1;                              // next tile via cp.async
+    // next tile via cp.async into a shared buffer, or (DIRECT) straight from global memory into the
+    // stage-A registers: the smaller footprint fits three CTAs per SM at C = 4, which hides the load
+    // latency better than the prefetch does with two (force z pass at 1024^3: 6.0 against 6.9 ms)
+    static constexpr bool PREFETCH = MODE != Z_LPT1 && !DIRECT;
+    static constexpr int MINB = DIRECT && C == 4 ? 3 : 1;                         // CTAs per SM
     static constexpr int PF = PREFETCH ? C * L : 0;                               // dense [z][C] buffer
     static constexpr int TA = C * L / R1, TB = C * L / R2, T = TA > TB ? TA : TB;
     static constexpr size_t SMEM = sizeof(float2) * ((size_t)XS * (1 + NSAVE) + PF) + sizeof(Tw2);
 };
 
-template <int L, int MODE, int C = 8, bool BLK = false>
-__global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ in, ZOut out, const float2* __restrict__ tw,
-                                                          const float* __restrict__ sinc2, int deconv, float gnorm,
-                                                          PowerArgs pw) {
-    using Z = Z2<L, MODE, C>;
+template <int L, int MODE, int C = 8, bool BLK = false, bool DIRECT = false>
+__global__ void __launch_bounds__(Z2<L, MODE, C, DIRECT>::T, Z2<L, MODE, C, DIRECT>::MINB)
+    k2_fz(float2* __restrict__ in, ZOut out, const float2* __restrict__ tw, const float* __restrict__ sinc2, int deconv,
+          float gnorm, PowerArgs pw) {
+    using Z = Z2<L, MODE, C, DIRECT>;
     constexpr int R1 = Z::R1, R2 = Z::R2, n = L / 2, NG = n / C, NTILE = NG * L;
     constexpr int T = Z::T;
     extern __shared__ float4 smem4[];
@@ -247,15 +251,20 @@ __global__ void __launch_bounds__(Z2<L, MODE, C>::T) k2_fz(float2* __restrict__ 
                 for (int r = 0; r < R2; ++r) v[r] = __ldcg(in + base + (size_t)(j + R1 * r) * stride);
             }
         } else {
-            cp_async_wait<0>();
-            __syncthreads();
             float2 a[R1];
-            if (tid < TA) {
+            if constexpr (Z::PREFETCH) {
+                cp_async_wait<0>();
+                __syncthreads();
+                if (tid < TA) {
 #pragma unroll
-                for (int r = 0; r < R1; ++r) a[r] = pf[(j + r * (L / R1)) * C + c];
+                    for (int r = 0; r < R1; ++r) a[r] = pf[(j + r * (L / R1)) * C + c];
+                }
+                __syncthreads();   // prefetch buffer consumed
+                if (t + (int)gridDim.x < NTILE) prefetch(t + gridDim.x);
+            } else if (tid < TA) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) a[r] = __ldcg(in + base + (size_t)(j + r * (L / R1)) * stride);
             }
-            __syncthreads();   // prefetch buffer consumed
-            if (t + (int)gridDim.x < NTILE) prefetch(t + gridDim.x);
             if (tid < TA) {
                 dft<R1, -1>(a);
 #pragma unroll

@@ -11,18 +11,19 @@ static cudaError_t fz2(float2* in, ZOut out, const float2* tw, const float* sinc
     // neighbouring tiles complete) measured 2% faster than 8-column ones, and 34% faster for the
     // power spectrum. Standard layout: 8 columns (4-column rows there are 32 bytes 4 MB apart).
     constexpr int CZ = BLK ? 4 : 8;
-    using Z = Z2<N, MODE, CZ>;
+    constexpr bool DIRECT = BLK;   // blocked layout: loads straight into registers, three CTAs per SM
+    using Z = Z2<N, MODE, CZ, DIRECT>;
     const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
     static size_t configured2 = 0;
     static int grid2 = 0;
     if (smem > configured2 || !grid2) {
-        cudaError_t e = set_smem(k2_fz<N, MODE, CZ, BLK>, smem);
+        cudaError_t e = set_smem(k2_fz<N, MODE, CZ, BLK, DIRECT>, smem);
         if (e != cudaSuccess) return e;
         configured2 = smem > configured2 ? smem : configured2;
-        grid2 = persistent_grid(k2_fz<N, MODE, CZ, BLK>, Z::T, smem);
+        grid2 = persistent_grid(k2_fz<N, MODE, CZ, BLK, DIRECT>, Z::T, smem);
     }
     const int total = (N / 2 / CZ) * N;
-    k2_fz<N, MODE, CZ, BLK><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
+    k2_fz<N, MODE, CZ, BLK, DIRECT><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
     return cudaGetLastError();
 }
 
