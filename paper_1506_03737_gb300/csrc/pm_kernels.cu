@@ -65,7 +65,16 @@ __global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict_
                                     StepCoef k, int drift) {
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
-    float4 P = pos[p];
+    // every load of the particle's own data is issued before the force loads that depend on its
+    // position, so the two sets are in flight together (streaming: each is used once per step)
+    const float4 P = __ldcs(pos + p);
+    float s1[3], s2[3], v[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        s1[j] = __ldcs(psi1 + j * np3 + p);
+        s2[j] = __ldcs(psi2 + j * np3 + p);
+        v[j] = __ldcs(mom + j * np3 + p);
+    }
     const Cic c = cic_setup(P, nm);
     const float s = 1.0f / 32768.0f;
     const float wx[2] = {(QONE - c.fx) * s, c.fx * s};
@@ -94,13 +103,11 @@ __global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict_
                    (int)((__float_as_uint(P.w) / ((unsigned)nm * (unsigned)nm)) % (unsigned)nm)};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float s1 = psi1[j * np3 + p], s2 = psi2[j * np3 + p];
         // kick (Eq. eq:vcola): p += K [F - D1 Psi1 - (D2 - D1^2) Psi2]
-        float v = mom[j * np3 + p];
-        v = fmaf(k.kick, f[j] - k.c1 * s1 - k.c2 * s2, v);
-        mom[j * np3 + p] = v;
+        v[j] = fmaf(k.kick, f[j] - k.c1 * s1[j] - k.c2 * s2[j], v[j]);
+        __stcs(mom + j * np3 + p, v[j]);
         // drift (Eq. eq:rcola): x += S p + dD1 Psi1 + dD2 Psi2
-        d[j] = drift ? fmaf(k.drift, v, fmaf(k.e1, s1, k.e2 * s2)) : 0.0f;
+        d[j] = drift ? fmaf(k.drift, v[j], fmaf(k.e1, s1[j], k.e2 * s2[j])) : 0.0f;
     }
     if (!drift) return;
     float o[3];
@@ -116,7 +123,7 @@ __global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict_
         o[j] = r;
     }
     const unsigned lin = (unsigned)cell[0] + (unsigned)nm * ((unsigned)cell[1] + (unsigned)nm * (unsigned)cell[2]);
-    pos[p] = make_float4(o[0], o[1], o[2], __uint_as_float(lin));
+    __stcs(pos + p, make_float4(o[0], o[1], o[2], __uint_as_float(lin)));
 }
 
 // Particles on the Lagrangian lattice (offset by half a PM cell), displaced by D1 Psi1 + D2 Psi2.
