@@ -34,11 +34,19 @@ ALG_BYTES_CELL = 80
 # Per-kernel algorithmic bytes per cell (mesh kernels) or particle (particle kernels).
 ALG_PHASE = {
     "poisson": ("cell", 12),     # z pass: read the half spectrum, write the two inverse-z bases
-    "fft_inv": ("cell", 44),     # inverse y (2 bases -> 3 spectra, 20 B) + inverse x (3 fields, 24 B)
+    "fft_inv": ("cell", 20),     # inverse y: read the 2 bases, write 3 spectra
+    "fft_inv_x": ("cell", 24),   # inverse x: read 3 half spectra, write 3 real force meshes
     "fft_fwd": ("cell", 12),     # forward passes: read int64 density, write half spectrum
-    "deposit": ("cell", 16),     # zero + atomic write-back of the int64 mesh (+16 B/particle below)
+    "deposit": ("cell", 16),     # atomic read-modify-write of the int64 mesh (+16 B/particle below)
     "gather": ("particle", 80),  # read pos, mom, psi1, psi2, write pos, mom (+12 B/cell below)
 }
+EXTRA = {"deposit": ("particle", 16), "gather": ("cell", 12)}
+# Single-kernel phases, and the DRAM bytes (read + write) ncu measured for each kernel at
+# 256^3 particles / 512^3 mesh (per launch, MB), scaled to other sizes with N_m = 2 N_p by the
+# cell count: force z pass 537.2 + 1016.5, inverse x 1610.7 + 1559.4, force y inverse
+# 1073.9 + 1546.4, gather 2494.6 + 454.1, deposit 1244.2 + 792.9.
+DRAM_512 = {"poisson": 1553.7e6, "fft_inv_x": 3170.1e6, "fft_inv": 2620.3e6, "gather": 2948.7e6,
+            "deposit": 2037.1e6}
 
 
 def parse():
@@ -386,16 +394,14 @@ def main():
     for name, (unit, b) in ALG_PHASE.items():
         n = max(int(phase_n[name]), 1)
         per_call[name] = phase_ms[name] / n
-    single = ["poisson", "gather"]
-    dom = max(single, key=lambda k: phase_ms[k])
+    dom = max(DRAM_512, key=lambda k: phase_ms[k])
+    units = {"cell": nm ** 3, "particle": np_ ** 3}
     unit, b = ALG_PHASE[dom]
-    nbytes = b * (nm ** 3 if unit == "cell" else np_ ** 3)
-    if dom == "gather":
-        nbytes += 12 * nm ** 3
+    nbytes = b * units[unit]
+    if dom in EXTRA:
+        nbytes += EXTRA[dom][1] * units[EXTRA[dom][0]]
     achieved = nbytes / (per_call[dom] / 1e3) / 1e9
-    # DRAM bytes (read + write) per cell of the force z pass from an ncu capture of the same
-    # kernel at 512^3 (548.2 MB + 1021.5 MB), scaled by the cell count; none for the gather.
-    traffic = 1569.7e6 / 512 ** 3 * nm ** 3 if dom == "poisson" else None
+    traffic = DRAM_512[dom] / 512 ** 3 * nm ** 3 if nm == 2 * np_ else None
     alg_step = ALG_BYTES_PARTICLE * np_ ** 3 + ALG_BYTES_CELL * nm ** 3
 
     line = {
@@ -410,7 +416,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs"},
-        "cola_step_ms": sum(phase_ms[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "gather"))
+        "cola_step_ms": sum(phase_ms[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather"))
                         / max(int(phase_n["gather"]), 1),
         "cola_step_roofline_frac": None,
         "phase_ms_per_mock": {k: v / args.steps for k, v in phase_ms.items()},

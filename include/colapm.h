@@ -179,10 +179,12 @@ enum {
     COLAPM_PHASE_DEPOSIT = 0,   /* zero + fixed-point CIC deposit                   */
     COLAPM_PHASE_FFT_FWD,       /* x and y forward passes of the density            */
     COLAPM_PHASE_POISSON,       /* z forward, Green/gradient/deconvolution, z inverse */
-    COLAPM_PHASE_FFT_INV,       /* y and x inverse passes of the three forces       */
+    COLAPM_PHASE_FFT_INV,       /* y inverse pass of the forces (both inverse passes
+                                   with the fused x-y engine)                       */
     COLAPM_PHASE_GATHER,        /* CIC gather + kick + drift                        */
     COLAPM_PHASE_ICS,           /* initial conditions                               */
     COLAPM_PHASE_POWER,         /* power-spectrum transform and binning             */
+    COLAPM_PHASE_FFT_INV_X,     /* x inverse pass of the three forces (c2r)         */
     COLAPM_PHASE_COUNT
 };
 int colapm_set_timing(colapm_ctx* ctx, int on);

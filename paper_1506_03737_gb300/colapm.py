@@ -12,7 +12,7 @@ import numpy as np
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libcolapm.so")
 
-PHASES = ["deposit", "fft_fwd", "poisson", "fft_inv", "gather", "ics", "power"]
+PHASES = ["deposit", "fft_fwd", "poisson", "fft_inv", "gather", "ics", "power", "fft_inv_x"]
 
 
 class ColapmError(RuntimeError):

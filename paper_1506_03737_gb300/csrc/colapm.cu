@@ -199,20 +199,24 @@ int compute_force(colapm_ctx* c) {
         CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream, c->two_stage,
                       use_blocked(c)));
     }
+    if (use_xy(c, 2)) {
+        Phase ph(c, COLAPM_PHASE_FFT_INV);
+        CKL(launch_xy_inv(c->nm, d, fs, 3, c->tw_m, c->xy_ring, c->xy_ctr, c->err, c->stream));
+        return COLAPM_OK;
+    }
+    const bool blk = use_blocked(c);
     {
         Phase ph(c, COLAPM_PHASE_FFT_INV);
-        if (use_xy(c, 2)) {
-            CKL(launch_xy_inv(c->nm, d, fs, 3, c->tw_m, c->xy_ring, c->xy_ctr, c->err, c->stream));
+        if (blk) {
+            CKL(launch_fy_force(c->nm, d, fs, c->tw_m, c->stream));   // bases -> three spectra
         } else {
-            const bool blk = use_blocked(c);
-            if (blk) {
-                CKL(launch_fy_force(c->nm, d, fs, c->tw_m, c->stream));   // bases -> three spectra
-            } else {
-                CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk));
-            }
-            CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk,
-                              blk ? reinterpret_cast<float2*>(c->Freal) : nullptr));
+            CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk));
         }
+    }
+    {
+        Phase ph(c, COLAPM_PHASE_FFT_INV_X);
+        CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk,
+                          blk ? reinterpret_cast<float2*>(c->Freal) : nullptr));
     }
     return COLAPM_OK;
 }

@@ -469,8 +469,8 @@ struct X2 {
     static constexpr int RA = F2<n>::R1, RB = F2<n>::R2;
     static constexpr int TA = 8 * n / RA, TB = 8 * n / RB, T = TA > TB ? TA : TB;
     static constexpr size_t SMEM = sizeof(float2) * (size_t)Xch<n, RA>::SIZE + sizeof(Tw2);
-    // inverse: plus two dense [8][n] staging buffers for the cp.async prefetch of the rows
-    static constexpr size_t SMEM_INV = SMEM + 2 * sizeof(float2) * 8 * (size_t)n;
+    // inverse: plus a dense [8][n] staging buffer for the cp.async prefetch of the rows
+    static constexpr size_t SMEM_INV = SMEM + sizeof(float2) * 8 * (size_t)n;
 };
 
 // forward r2c: in = int64 density pairs (I64, converted to rho * scale - 1) or float reals.
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ i
 // With BLK the spectra are read in the blocked layout and the real rows written to `dst` (same field
 // stride), a separate array; otherwise dst == data and the pass is in place.
 template <int n, bool BLK = false>
-__global__ void __launch_bounds__(X2<n>::T) k2_fx_inv(float2* __restrict__ data, size_t fstride,
+__global__ void __launch_bounds__(X2<n>::T, 3) k2_fx_inv(float2* __restrict__ data, size_t fstride,
                                                        const float2* __restrict__ tw, int items_per_field,
                                                        int nfields, float2* __restrict__ dst) {
     using X = X2<n>;
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_inv(float2* __restrict__ data,
     extern __shared__ float4 smem4[];
     float2* xb = reinterpret_cast<float2*>(smem4);
     Tw2* tws = reinterpret_cast<Tw2*>(xb + Xch<n, RA>::SIZE);
-    float2* stg = reinterpret_cast<float2*>(tws + 1);   // 2 x [8][n]
+    float2* stg = reinterpret_cast<float2*>(tws + 1);   // [8][n]
     load_tw2<n, N>(tws, tw, T);
     const int tid = threadIdx.x;
     const int nitems = items_per_field * nfields;
@@ -588,48 +588,31 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_inv(float2* __restrict__ data,
     int it = 0;
     for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++it) {
         float2* d = gptr(t);
-        const float2* rows = stg + (it & 1) * 8 * n;
+        const float2* rows = stg;
         cp_async_wait<0>();
         __syncthreads();
-        if (t + (int)gridDim.x < nitems) prefetch(t + gridDim.x, (it + 1) & 1);
-        constexpr int H = n / 2 + 1;
-        for (int e = tid; e < 8 * H; e += T) {   // Z'[k], Z'[n-k] from X[k], X[n-k] (X[n] = 0)
-            const int c = e / H, k = e % H;
-            const float2* row = rows + c * n;
-            const float2 xk = row[k];
-            if (k == 0) {
-                xb[Xch<n, RA>::at(c, 0)] = make_float2(xk.x - xk.y, xk.y + xk.x);   // X0 + i X0
-                continue;
-            }
-            const int k2 = n - k;
-            const float2 xk2 = row[k2];
-            {
-                const float2 xc = cconj(xk2);
-                const float2 E = cadd(xk, xc);
-                const float2 O = cmul(csub(xk, xc), cconj(tw[k]));
-                xb[Xch<n, RA>::at(c, k)] = make_float2(E.x - O.y, E.y + O.x);
-            }
-            if (k2 != k) {
-                const float2 xc = cconj(xk);
-                const float2 E = cadd(xk2, xc);
-                const float2 O = cmul(csub(xk2, xc), cconj(tw[k2]));
-                xb[Xch<n, RA>::at(c, k2)] = make_float2(E.x - O.y, E.y + O.x);
-            }
-        }
-        __syncthreads();
-        float2 v[RA];
+        // stage A reads its inputs Z'[k] = E + i O straight from the staged rows, with
+        // E = X[k] + conj X[n-k], O = (X[k] - conj X[n-k]) conj w^k and X[n] = 0
         const int ca = tid / (n / RA), ja = tid % (n / RA);
         if (tid < X::TA) {
+            const float2* row = rows + ca * n;
+            float2 v[RA];
 #pragma unroll
-            for (int r = 0; r < RA; ++r) v[r] = xb[Xch<n, RA>::at(ca, ja + r * (n / RA))];
+            for (int r = 0; r < RA; ++r) {
+                const int k = ja + r * (n / RA);
+                const float2 xk = row[k];
+                const float2 xm = row[(n - k) & (n - 1)];
+                const float2 xc = k == 0 ? make_float2(0.0f, 0.0f) : cconj(xm);
+                const float2 E = cadd(xk, xc);
+                const float2 O = cmul(csub(xk, xc), cconj(tw[k]));
+                v[r] = make_float2(E.x - O.y, E.y + O.x);
+            }
             dft<RA, +1>(v);
-        }
-        __syncthreads();
-        if (tid < X::TA) {
 #pragma unroll
             for (int r = 0; r < RA; ++r) xb[Xch<n, RA>::at(ca, ja * RA + r)] = v[r];
         }
         __syncthreads();
+        if (t + (int)gridDim.x < nitems) prefetch(t + gridDim.x, 0);   // staging free: overlaps stage B
         if (tid < X::TB) {
             const int c = tid / RA, j = tid % RA;
             float2 u[RB];
@@ -637,7 +620,7 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_inv(float2* __restrict__ data,
 #pragma unroll
             for (int r = 0; r < RB; ++r) d[(size_t)c * n + j + RA * r] = u[r];
         }
-        __syncthreads();
+        // no barrier: the next tile's stage A writes xb only after the wait + barrier at its top
     }
     cp_async_wait<0>();
 }
