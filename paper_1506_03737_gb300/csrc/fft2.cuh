@@ -325,20 +325,20 @@ __global__ void __launch_bounds__(Z2<L, MODE, C, DIRECT>::T, Z2<L, MODE, C, DIRE
         } else {
             // bases: A = g X, B = k_z A (, C = k_z^2 A); g = gnorm / (k^2 [W^d]), 0 on excluded modes
             if (tid < TB) {
+                const int nxy2 = nx * nx + ny * ny;                                   // per column
+                const float wxy = MODE == Z_FORCE && deconv ? sinc2[nx] * sinc2[ky] : 1.0f;
 #pragma unroll
                 for (int r = 0; r < R2; ++r) {
                     const int z = j + R1 * r;
                     const int nz = sbin(z, L);
-                    float g = 0.0f;
-                    if (!nyq_y && z != L / 2 && (nx | ny | nz) != 0) {
-                        const float k2 = kf * kf * (float)(nx * nx + ny * ny + nz * nz);
-                        float w = 1.0f;
-                        if (MODE == Z_FORCE && deconv) {
-                            w = sinc2[nx] * sinc2[ky] * sinc2[z];
-                            if (deconv == 2) w *= w;
-                        }
-                        g = gnorm / (k2 * w);
+                    const int n2 = nxy2 + nz * nz;   // 0 only at k = 0
+                    float w = 1.0f;
+                    if (MODE == Z_FORCE && deconv) {
+                        w = wxy * sinc2[z];
+                        if (deconv == 2) w *= w;
                     }
+                    // fast division (within 2 ulp; k^2 W is far from the range where it flushes)
+                    const float g = !nyq_y && z != L / 2 && n2 != 0 ? __fdividef(gnorm, kf * kf * (float)n2 * w) : 0.0f;
                     v[r] = cscale(v[r], g);
                     const float kz = kf * (float)nz;
                     save[Xch<L, R1, C>::at(c, j + R1 * r)] = cscale(v[r], kz);
@@ -518,33 +518,30 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ i
             for (int r = 0; r < RA; ++r) xb[Xch<n, RA>::at(c, j * RA + r)] = v[r];
         }
         __syncthreads();
-        if (tid < X::TB) {   // stage B in place: Z[j + RA r]
+        if (tid < X::TB) {   // stage B: Z[j + RA r], then X[k] for the same k = j + RA r
+            static_assert(RA == 16 || RA == 32, "the partner of a task must be in its warp");
             const int c = tid / RA, j = tid % RA;
             float2 v[RB];
             stage_b<n, RA, RB, -1>(xb, tws, c, j, v);
-#pragma unroll
-            for (int r = 0; r < RB; ++r) xb[Xch<n, RA>::at(c, j + RA * r)] = v[r];
-        }
-        __syncthreads();
-        constexpr int H = n / 2 + 1;
-        for (int e = tid; e < 8 * H; e += X::T) {
-            const int c = e / H, k = e % H, k2 = (n - k) % n;
-            const float2 a = xb[Xch<n, RA>::at(c, k)], b = xb[Xch<n, RA>::at(c, k2)];
+            // X[k] needs Z[n - k] too: for j > 0 that is element RB - 1 - r of task RA - j (same
+            // line, same warp); for j = 0 it is this task's own element (RB - r) mod RB
+            const int lane = threadIdx.x & 31;
+            const int partner = (lane & ~(RA - 1)) | ((RA - j) & (RA - 1));
             const int y = (int)((row0 + c) % N), z = (int)((row0 + c) / N);
-            {   // X[k] from Z[k] = a, Z[n-k] = b; w^k = exp(-2 pi i k / N) = tw[k]
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const float bx = __shfl_sync(0xffffffffu, v[RB - 1 - r].x, partner);
+                const float by = __shfl_sync(0xffffffffu, v[RB - 1 - r].y, partner);
+                const float2 a = v[r], b = j == 0 ? v[(RB - r) % RB] : make_float2(bx, by);
+                const int k = j + RA * r;
+                // X[k] from Z[k] = a, Z[n-k] = b; w^k = exp(-2 pi i k / N) = tw[k]
                 const float2 bc = cconj(b);
                 const float2 E = cscale(cadd(a, bc), 0.5f);
                 const float2 d = csub(a, bc);
                 out[hs_index<N, BLK>(k, y, z)] = cadd(E, cmul(tw[k], make_float2(0.5f * d.y, -0.5f * d.x)));
             }
-            if (k != 0 && k2 != k) {
-                const float2 ac = cconj(a);
-                const float2 E = cscale(cadd(b, ac), 0.5f);
-                const float2 d = csub(b, ac);
-                out[hs_index<N, BLK>(k2, y, z)] = cadd(E, cmul(tw[k2], make_float2(0.5f * d.y, -0.5f * d.x)));
-            }
         }
-        __syncthreads();
+        __syncthreads();   // exchange buffer free for the next tile's stage A
     }
     if constexpr (I64) {
         if (over) atomicOr(err, 1);
