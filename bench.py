@@ -43,10 +43,10 @@ ALG_PHASE = {
 EXTRA = {"deposit": ("particle", 16), "gather": ("cell", 12)}
 # Single-kernel phases, and the DRAM bytes (read + write) ncu measured for each kernel at
 # 256^3 particles / 512^3 mesh (per launch, MB), scaled to other sizes with N_m = 2 N_p by the
-# cell count: force z pass 537.2 + 1016.5, inverse x 1610.7 + 1559.4, force y inverse
-# 1073.9 + 1546.4, gather 2494.6 + 454.1, deposit 1244.2 + 792.9.
-DRAM_512 = {"poisson": 1553.7e6, "fft_inv_x": 3170.1e6, "fft_inv": 2620.3e6, "gather": 2948.7e6,
-            "deposit": 2037.1e6}
+# cell count: force z pass 538.8 + 1017.2, inverse x 1610.7 + 1561.6, force y inverse
+# 1073.9 + 1546.3, gather 2494.7 + 454.1, deposit 1243.8 + 792.8.
+DRAM_512 = {"poisson": 1556.0e6, "fft_inv_x": 3172.3e6, "fft_inv": 2620.2e6, "gather": 2948.8e6,
+            "deposit": 2036.6e6}
 
 
 def parse():
