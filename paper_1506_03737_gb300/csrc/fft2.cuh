@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(Z2<L, MODE, C, DIRECT>::T, Z2<L, MODE, C, DIRE
             const int pc = tid % C, z0 = (tid / C) * PER, px = kx0 + pc;
             if (!nyq_y) {
                 int rb = -1;
-                double rp = 0.0, rk = 0.0;   // FP64 sums of FP32 per-mode values
+                float rp = 0.0f, rk = 0.0f;   // FP32 sums over one run of at most a few dozen modes, flushed to FP64 bins
                 unsigned rc = 0;
                 const float mult = px == 0 ? 1.0f : 2.0f;   // conjugate twin with k_x -> -k_x
 #pragma unroll 8
@@ -299,24 +299,24 @@ __global__ void __launch_bounds__(Z2<L, MODE, C, DIRECT>::T, Z2<L, MODE, C, DIRE
                     if (b < 0) continue;
                     if (b != rb) {
                         if (rb >= 0) {
-                            atomicAdd(&psum[rb], rp);
-                            atomicAdd(&ksum[rb], rk);
+                            atomicAdd(&psum[rb], (double)rp);
+                            atomicAdd(&ksum[rb], (double)rk);
                             atomicAdd(&cnt[rb], (unsigned long long)rc);
                         }
                         rb = b;
-                        rp = 0.0;
-                        rk = 0.0;
+                        rp = 0.0f;
+                        rk = 0.0f;
                         rc = 0;
                     }
                     const float2 q = xb[Xch<L, R1, C>::at(pc, z)];
                     const float w = sinc2[px] * sinc2[ky] * sinc2[z];
-                    rp += (double)(mult * (q.x * q.x + q.y * q.y) * pw.pnorm / (w * w));
-                    rk += (double)(mult * pw.kf * sqrtf((float)n2));
+                    rp += __fdividef(mult * (q.x * q.x + q.y * q.y) * pw.pnorm, w * w);
+                    rk += mult * pw.kf * sqrtf((float)n2);
                     rc += px == 0 ? 1u : 2u;
                 }
                 if (rb >= 0) {
-                    atomicAdd(&psum[rb], rp);
-                    atomicAdd(&ksum[rb], rk);
+                    atomicAdd(&psum[rb], (double)rp);
+                    atomicAdd(&ksum[rb], (double)rk);
                     atomicAdd(&cnt[rb], (unsigned long long)rc);
                 }
             }

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
             const int c = threadIdx.x % 8, z0 = (threadIdx.x / 8) * PER;
             const int nx = kx0 + c;
             int rb = -1;
-            double rp = 0.0, rk = 0.0;   // FP64 sums of FP32 per-mode values
+            float rp = 0.0f, rk = 0.0f;   // FP32 sums over one run of at most a few dozen modes, flushed to FP64 bins
             unsigned rc = 0;
             const float mult = nx == 0 ? 1.0f : 2.0f;    // conjugate twin with k_x -> -k_x
             if (!nyq_y) {
@@ -419,25 +419,25 @@ __global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
                     if (b < 0) continue;
                     if (b != rb) {
                         if (rb >= 0) {
-                            atomicAdd(&psum[rb], rp);
-                            atomicAdd(&ksum[rb], rk);
+                            atomicAdd(&psum[rb], (double)rp);
+                            atomicAdd(&ksum[rb], (double)rk);
                             atomicAdd(&cnt[rb], (unsigned long long)rc);
                         }
                         rb = b;
-                        rp = 0.0;
-                        rk = 0.0;
+                        rp = 0.0f;
+                        rk = 0.0f;
                         rc = 0;
                     }
                     const float2 v = cur[CT<L>::a2(z, c)];
                     const float w = sinc2[nx] * sinc2[ky] * sinc2[z];
-                    rp += (double)(mult * (v.x * v.x + v.y * v.y) * pw.pnorm / (w * w));
-                    rk += (double)(mult * pw.kf * sqrtf((float)n2));
+                    rp += __fdividef(mult * (v.x * v.x + v.y * v.y) * pw.pnorm, w * w);
+                    rk += mult * pw.kf * sqrtf((float)n2);
                     rc += nx == 0 ? 1u : 2u;
                 }
             }
             if (rb >= 0) {
-                atomicAdd(&psum[rb], rp);
-                atomicAdd(&ksum[rb], rk);
+                atomicAdd(&psum[rb], (double)rp);
+                atomicAdd(&ksum[rb], (double)rk);
                 atomicAdd(&cnt[rb], (unsigned long long)rc);
             }
             __syncthreads();
