@@ -305,3 +305,21 @@ def test_checkpoint_resume_is_bit_exact(C):
     finally:
         a.close()
         b.close()
+
+
+def test_phase_timing_counts(C):
+    """Each COLA step runs every step phase once (the x inverse timed on its own); reading clears."""
+    s = Sim(C, np=32, nm=64, box=256.0, n_steps=4)
+    try:
+        C.colapm_set_timing(s.ctx, True)
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, 2)
+        ms, n = C.colapm_get_timing(s.ctx)
+        assert set(ms) == set(C.PHASES)
+        for ph in ("deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather"):
+            assert n[ph] == 2 and ms[ph] > 0.0, ph
+        assert n["ics"] == 1 and n["power"] == 0
+        ms2, n2 = C.colapm_get_timing(s.ctx)
+        assert all(v == 0 for v in n2.values()) and all(v == 0.0 for v in ms2.values())
+    finally:
+        s.close()
