@@ -374,11 +374,16 @@ def main():
         nh = torch.empty(nbins, dtype=torch.int64, pin_memory=True)
         posh = torch.empty((np_ ** 3, 3), dtype=torch.float32, pin_memory=True)
         momh = torch.empty((np_ ** 3, 3), dtype=torch.float32, pin_memory=True)
+        # the catalogue copy of one mock overlaps the next mock (copy stream, device staging array)
+        mock(mock_seed(rank, 3, 0), kh, ph, nh)      # untimed: allocates the staging array
+        C.colapm_get_particles_async(ctx, posh, momh)
+        C.colapm_wait_particles(ctx)
         barrier()
         t0 = time.perf_counter()
         for s in range(args.steps):
             mock(mock_seed(rank, 2, s), kh, ph, nh)
-            C.colapm_get_particles(ctx, posh, momh)
+            C.colapm_get_particles_async(ctx, posh, momh)
+        C.colapm_wait_particles(ctx)
         torch.cuda.synchronize()
         barrier()
         secs = max_over_ranks(time.perf_counter() - t0)
@@ -386,7 +391,9 @@ def main():
         e2e = {"value": updates / secs, "unit": "particle-updates/s", "h2d_bytes_per_step": 8,
                "d2h_bytes_per_step": d2h,
                "note": "inputs are the seed and parameters (8 B per mock); outputs are P(k) and the final "
-                       "particle catalogue (positions and momenta, float32 xyz) copied to pinned host memory"}
+                       "particle catalogue (positions and momenta, float32 xyz) copied to pinned host memory, "
+                       "each mock's catalogue copy overlapping the next mock; all copies landed before the "
+                       "clock stops"}
 
     # roofline of the dominant kernel: the phase with the largest share that is one kernel
     hbm, peak_src = peaks()

@@ -123,6 +123,19 @@ int colapm_power(colapm_ctx* ctx, int nbins, double kmin, double kmax,
  * may be NULL. Host or device. Synchronises. */
 int colapm_get_particles(colapm_ctx* ctx, float* pos, float* mom);
 
+/* The same catalogue into host memory (3 * Np^3 floats each, caller-owned; page-locked memory lets
+ * the copy run asynchronously), without waiting for it: the particles are exported on the
+ * context's stream into a device staging array of the context (6 * Np^3 floats, allocated on the
+ * first call, COLAPM_E_NOMEM if that fails) and copied out on a separate copy stream, so the copy
+ * overlaps the work the caller enqueues next (e.g. the next mock). The host arrays must not be
+ * read or freed before colapm_wait_particles returns. A later call waits on the device (not the
+ * host) for the previous copy to leave the staging array. Either pointer may be NULL. */
+int colapm_get_particles_async(colapm_ctx* ctx, float* pos, float* mom);
+
+/* Block the host until the copy of the last colapm_get_particles_async has landed; then report
+ * any pending device error like the synchronising calls. */
+int colapm_wait_particles(colapm_ctx* ctx);
+
 /* Raw particle state: integer mesh cell (xyz int32), offset in [0,1) cells (xyz float) and
  * momentum in mesh units (xyz float, Mpc/h divided by the cell size). Any pointer may be NULL.
  * Host or device. Synchronises. */

@@ -57,6 +57,8 @@ def _load():
         "colapm_finalize": (I, [P]),
         "colapm_power": (I, [P, I, D, D, P, P, P]),
         "colapm_get_particles": (I, [P, P, P]),
+        "colapm_get_particles_async": (I, [P, P, P]),
+        "colapm_wait_particles": (I, [P]),
         "colapm_get_state": (I, [P, P, P, P]),
         "colapm_set_state": (I, [P, P, P, P]),
         "colapm_get_density": (I, [P, P]),
@@ -177,6 +179,15 @@ def colapm_power(ctx, nbins, kmin=0.0, kmax=0.0, k_out=None, p_out=None, n_out=N
 def colapm_get_particles(ctx, pos=None, mom=None):
     _check(LIB.colapm_get_particles(ctx, _ptr(pos), _ptr(mom)), "colapm_get_particles")
     return pos, mom
+
+
+def colapm_get_particles_async(ctx, pos=None, mom=None):
+    _check(LIB.colapm_get_particles_async(ctx, _ptr(pos), _ptr(mom)), "colapm_get_particles_async")
+    return pos, mom
+
+
+def colapm_wait_particles(ctx):
+    _check(LIB.colapm_wait_particles(ctx), "colapm_wait_particles")
 
 
 def colapm_get_state(ctx, cell=None, offset=None, mom=None):

@@ -28,6 +28,10 @@ struct colapm_ctx {
     float* psi1 = nullptr;               // 3 np^3, cells
     float* psi2 = nullptr;               // 3 np^3, cells
     float* scratch = nullptr;            // 9 np^3 (IC spectra and phi_ij; staging for state I/O)
+    float* xfer = nullptr;               // 6 np^3: staging of the asynchronous catalogue copy (lazy)
+    cudaStream_t xfer_stream = nullptr;  // its copy stream
+    cudaEvent_t xfer_ready = nullptr, xfer_done = nullptr;
+    bool xfer_pending = false;           // a copy out of xfer may still be running
     float2* tw_m = nullptr;              // exp(-2 pi i t / nm)
     float2* tw_p = nullptr;              // exp(-2 pi i t / np)
     float* sinc2_m = nullptr;            // sinc^2(pi n / nm) per FFT bin
@@ -105,8 +109,9 @@ bool is_device_ptr(const void* p) {
 }
 
 void free_all(colapm_ctx* c) {
+    if (c->xfer_stream) cudaStreamSynchronize(c->xfer_stream);
     void* ptrs[] = {c->rho, c->F, c->Freal, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
-                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed, c->xy_ring, c->xy_ctr};
+                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed, c->xy_ring, c->xy_ctr, c->xfer};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& v : c->ev)
@@ -114,6 +119,9 @@ void free_all(colapm_ctx* c) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
+    if (c->xfer_ready) cudaEventDestroy(c->xfer_ready);
+    if (c->xfer_done) cudaEventDestroy(c->xfer_done);
+    if (c->xfer_stream) cudaStreamDestroy(c->xfer_stream);
 }
 
 std::vector<float2> twiddles(int n) {
@@ -567,6 +575,42 @@ int colapm_get_particles(colapm_ctx* c, float* pos, float* mom) {
     CKL(launch_export_particles(c->pos, c->mom, c->np3, c->nm, cell, dp, dm, c->stream));
     if (pos && dp != pos) copy_out(c, pos, dp, 3 * c->np3 * sizeof(float));
     if (mom && dm != mom) copy_out(c, mom, dm, 3 * c->np3 * sizeof(float));
+    return pending_error(c);
+}
+
+int colapm_get_particles_async(colapm_ctx* c, float* pos, float* mom) {
+    if (!c) return COLAPM_E_ARG;
+    if (!c->has_ics) return COLAPM_E_STATE;
+    if (!c->xfer) {
+        if (dalloc(&c->xfer, 6 * c->np3) != cudaSuccess) {
+            c->xfer = nullptr;
+            cudaGetLastError();
+            return COLAPM_E_NOMEM;
+        }
+        CK(cudaStreamCreateWithFlags(&c->xfer_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->xfer_ready, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->xfer_done, cudaEventDisableTiming));
+    }
+    if (c->xfer_pending) CK(cudaStreamWaitEvent(c->stream, c->xfer_done, 0));   // staging array free
+    const float cell = (float)(c->prm.box / c->nm);
+    float* dp = c->xfer;
+    float* dm = c->xfer + 3 * c->np3;
+    CKL(launch_export_particles(c->pos, c->mom, c->np3, c->nm, cell, dp, dm, c->stream));
+    CK(cudaEventRecord(c->xfer_ready, c->stream));
+    CK(cudaStreamWaitEvent(c->xfer_stream, c->xfer_ready, 0));
+    if (pos) CK(cudaMemcpyAsync(pos, dp, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->xfer_stream));
+    if (mom) CK(cudaMemcpyAsync(mom, dm, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->xfer_stream));
+    CK(cudaEventRecord(c->xfer_done, c->xfer_stream));
+    c->xfer_pending = true;
+    return COLAPM_OK;
+}
+
+int colapm_wait_particles(colapm_ctx* c) {
+    if (!c) return COLAPM_E_ARG;
+    if (c->xfer_pending) {
+        CK(cudaEventSynchronize(c->xfer_done));
+        c->xfer_pending = false;
+    }
     return pending_error(c);
 }
 

@@ -323,3 +323,30 @@ def test_phase_timing_counts(C):
         assert all(v == 0 for v in n2.values()) and all(v == 0.0 for v in ms2.values())
     finally:
         s.close()
+
+
+def test_async_catalogue_copy_matches_sync(C):
+    """colapm_get_particles_async delivers the catalogue of the moment it was called, even when the
+    caller steps the particles on before waiting; a second call reuses the staging array."""
+    import torch
+    s = Sim(C, np=32, nm=64, box=256.0, n_steps=4, seed=5)
+    try:
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, 1)
+        n = s.np ** 3
+        ref_p, ref_m = np.empty((n, 3), np.float32), np.empty((n, 3), np.float32)
+        C.colapm_get_particles(s.ctx, ref_p, ref_m)
+        pos = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+        mom = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+        C.colapm_get_particles_async(s.ctx, pos, mom)
+        C.colapm_step(s.ctx, 1)                      # moves the particles while the copy may run
+        C.colapm_wait_particles(s.ctx)
+        assert np.array_equal(pos.numpy(), ref_p) and np.array_equal(mom.numpy(), ref_m)
+        ref2_p = np.empty((n, 3), np.float32)
+        C.colapm_get_particles(s.ctx, ref2_p, None)
+        assert not np.array_equal(ref2_p, ref_p)
+        C.colapm_get_particles_async(s.ctx, pos, None)
+        C.colapm_wait_particles(s.ctx)
+        assert np.array_equal(pos.numpy(), ref2_p)
+    finally:
+        s.close()
