@@ -423,9 +423,9 @@ def main():
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs"},
-        # one call of each step phase (the deposit and forward passes also run once more per mock
-        # for P(k), so per-call averages, not totals over the gather count)
-        "cola_step_ms": sum(per_call[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather")),
+        # all step phases over the steps (P(k) times its deposit and forward passes as its own phase)
+        "cola_step_ms": sum(phase_ms[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather"))
+                        / max(int(phase_n["gather"]), 1),
         "cola_step_roofline_frac": None,
         "phase_ms_per_mock": {k: v / args.steps for k, v in phase_ms.items()},
         "clocks": clk.summary(),

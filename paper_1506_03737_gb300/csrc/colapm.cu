@@ -46,6 +46,7 @@ struct colapm_ctx {
     bool two_stage = true;               // FFT engine for 256/512/1024 lines (autotuned)
     int fused = 0;                       // fused x-y passes where supported: bit 0 forward, bit 1 inverse (autotuned)
     bool rho_clean = false;              // rho is all zero (the forward x pass clears it as it reads)
+    int phase_mute = 0;                  // > 0: phases nested in another phase are not timed
     float2* xy_ring = nullptr;           // L2-resident ring of intermediate planes of the fused passes
     int* xy_ctr = nullptr;               // their work ticket and per-plane completion counters
     int block = 256;                     // particle-kernel block size (autotuned)
@@ -84,7 +85,7 @@ struct Phase {   // CUDA-event bracket of one phase when timing is on
     int ph;
     cudaEvent_t b = nullptr, e = nullptr;
     Phase(colapm_ctx* ctx, int phase) : c(ctx), ph(phase) {
-        if (!c->timing) return;
+        if (!c->timing || c->phase_mute) return;
         if (cudaEventCreate(&b) == cudaSuccess && cudaEventCreate(&e) == cudaSuccess) cudaEventRecord(b, c->stream);
     }
     ~Phase() {
@@ -507,14 +508,21 @@ int power_prepare(colapm_ctx* c, int nbins, double kmin, double kmax) {
 }
 
 // Deposit, forward transform and bin into the device accumulators (no host synchronisation).
+struct PhaseMute {   // time the nested deposit and forward passes under the enclosing phase
+    colapm_ctx* c;
+    explicit PhaseMute(colapm_ctx* x) : c(x) { ++c->phase_mute; }
+    ~PhaseMute() { --c->phase_mute; }
+};
+
 int power_enqueue(colapm_ctx* c, int nbins) {
     const double box = c->prm.box;
+    Phase ph(c, COLAPM_PHASE_POWER);   // all of P(k), its deposit and forward passes included
+    PhaseMute mute(c);
     CK(cudaMemsetAsync(c->pw_acc, 0, (size_t)3 * nbins * sizeof(double), c->stream));
     int r = deposit(c);
     if (r) return r;
     r = density_xy(c);
     if (r) return r;
-    Phase ph(c, COLAPM_PHASE_POWER);
     PowerArgs pw{};
     pw.n2_lo = c->pw_bin;
     pw.kf = (float)(2.0 * M_PI / box);

@@ -319,6 +319,10 @@ def test_phase_timing_counts(C):
         for ph in ("deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather"):
             assert n[ph] == 2 and ms[ph] > 0.0, ph
         assert n["ics"] == 1 and n["power"] == 0
+        kd = np.empty(16)
+        C.colapm_power(s.ctx, 16, 0.0, 0.0, kd, np.empty(16), np.empty(16, np.int64))
+        ms, n = C.colapm_get_timing(s.ctx)
+        assert n["power"] == 1 and n["deposit"] == 0 and n["fft_fwd"] == 0   # P(k) timed as one phase
         ms2, n2 = C.colapm_get_timing(s.ctx)
         assert all(v == 0 for v in n2.values()) and all(v == 0.0 for v in ms2.values())
     finally:
@@ -350,3 +354,4 @@ def test_async_catalogue_copy_matches_sync(C):
         assert np.array_equal(pos.numpy(), ref2_p)
     finally:
         s.close()
+
