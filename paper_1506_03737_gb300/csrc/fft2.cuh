@@ -582,9 +582,10 @@ __global__ void __launch_bounds__(X2<n>::T) k2_fx_fwd(const void* __restrict__ i
 }
 
 // inverse c2r in place on `nfields` arrays; the next tile's rows are prefetched into a dense
-// [8][n] staging buffer with 16-byte cp.async while the current one is transformed.
-// With BLK the spectra are read in the blocked layout and the real rows written to `dst` (same field
-// stride), a separate array; otherwise dst == data and the pass is in place.
+// [8][n] staging buffer with 16-byte cp.async as soon as stage A has read the current one, so the
+// copy overlaps stage B. With BLK the spectra are read in the blocked layout and the real rows
+// written to `dst` (same field stride), a separate array; otherwise dst == data and the pass is in
+// place.
 template <int n, bool BLK = false>
 __global__ void __launch_bounds__(X2<n>::T, 3) k2_fx_inv(float2* __restrict__ data, size_t fstride,
                                                        const float2* __restrict__ tw, int items_per_field,
@@ -599,9 +600,9 @@ __global__ void __launch_bounds__(X2<n>::T, 3) k2_fx_inv(float2* __restrict__ da
     const int tid = threadIdx.x;
     const int nitems = items_per_field * nfields;
     auto gptr = [&](int t) { return dst + (size_t)(t / items_per_field) * fstride + (size_t)(t % items_per_field) * 8 * n; };
-    auto prefetch = [&](int t, int slot) {
-        float2* d = stg + slot * 8 * n;
-        if constexpr (BLK) {   // 8 rows of one plane: per 8-column block, 8 rows x 64 B contiguous
+    auto prefetch = [&](int t) {
+        float2* d = stg;
+        if constexpr (BLK) {   // 8 rows of one plane (one row group): a 512-byte run per 8-column block
             const int row0 = (t % items_per_field) * 8, y0 = row0 % N, z = row0 / N;
             const float2* g = data + (size_t)(t / items_per_field) * fstride;
             for (int e = tid; e < 8 * n / 2; e += T) {
@@ -614,9 +615,8 @@ __global__ void __launch_bounds__(X2<n>::T, 3) k2_fx_inv(float2* __restrict__ da
         }
         cp_async_commit();
     };
-    if (blockIdx.x < nitems) prefetch(blockIdx.x, 0);
-    int it = 0;
-    for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++it) {
+    if (blockIdx.x < nitems) prefetch(blockIdx.x);
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
         float2* d = gptr(t);
         const float2* rows = stg;
         cp_async_wait<0>();
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(X2<n>::T, 3) k2_fx_inv(float2* __restrict__ da
             for (int r = 0; r < RA; ++r) xb[Xch<n, RA>::at(ca, ja * RA + r)] = v[r];
         }
         __syncthreads();
-        if (t + (int)gridDim.x < nitems) prefetch(t + gridDim.x, 0);   // staging free: overlaps stage B
+        if (t + (int)gridDim.x < nitems) prefetch(t + gridDim.x);   // staging free: overlaps stage B
         if (tid < X::TB) {
             const int c = tid / RA, j = tid % RA;
             float2 u[RB];
