@@ -49,6 +49,23 @@ DRAM_512 = {"poisson": 1556.0e6, "fft_inv_x": 3172.3e6, "fft_inv": 2620.2e6, "ga
             "deposit": 2036.6e6}
 
 
+def roofline(phase_ms, phase_n, np_, nm, hbm):
+    """Roofline object of the dominant kernel: the single-kernel phase with the largest total time.
+    achieved = its algorithmic bytes per call / its mean call time; traffic = the ncu DRAM bytes
+    per call measured at 512^3, scaled by the cell count (None off the N_m = 2 N_p family)."""
+    dom = max(DRAM_512, key=lambda k: phase_ms[k])
+    units = {"cell": nm ** 3, "particle": np_ ** 3}
+    unit, b = ALG_PHASE[dom]
+    nbytes = b * units[unit]
+    if dom in EXTRA:
+        nbytes += EXTRA[dom][1] * units[EXTRA[dom][0]]
+    per_call_ms = phase_ms[dom] / max(int(phase_n[dom]), 1)
+    achieved = nbytes / (per_call_ms / 1e3) / 1e9
+    traffic = DRAM_512[dom] / 512 ** 3 * nm ** 3 if nm == 2 * np_ else None
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic, "alg_bytes": nbytes}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,20 +412,9 @@ def main():
                        "each mock's catalogue copy overlapping the next mock; all copies landed before the "
                        "clock stops"}
 
-    # roofline of the dominant kernel: the phase with the largest share that is one kernel
     hbm, peak_src = peaks()
-    per_call = {}
-    for name, (unit, b) in ALG_PHASE.items():
-        n = max(int(phase_n[name]), 1)
-        per_call[name] = phase_ms[name] / n
-    dom = max(DRAM_512, key=lambda k: phase_ms[k])
-    units = {"cell": nm ** 3, "particle": np_ ** 3}
-    unit, b = ALG_PHASE[dom]
-    nbytes = b * units[unit]
-    if dom in EXTRA:
-        nbytes += EXTRA[dom][1] * units[EXTRA[dom][0]]
-    achieved = nbytes / (per_call[dom] / 1e3) / 1e9
-    traffic = DRAM_512[dom] / 512 ** 3 * nm ** 3 if nm == 2 * np_ else None
+    roof = roofline(phase_ms, phase_n, np_, nm, hbm)
+    roof["peak_source"] = f"{peak_src} hbm_gbs"
     alg_step = ALG_BYTES_PARTICLE * np_ ** 3 + ALG_BYTES_CELL * nm ** 3
 
     line = {
@@ -421,8 +427,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (particle state and meshes ~35 GB)"},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_source": f"{peak_src} hbm_gbs"},
+        "roofline": roof,
         # all step phases over the steps (P(k) times its deposit and forward passes as its own phase)
         "cola_step_ms": sum(phase_ms[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather"))
                         / max(int(phase_n["gather"]), 1),
