@@ -189,14 +189,15 @@ int colapm_load_state(colapm_ctx* ctx, const void* buf, size_t n);
  * of the COLAPM_PHASE_COUNT phases, the summed milliseconds and the launch count, then
  * clears them (synchronises). */
 enum {
-    COLAPM_PHASE_DEPOSIT = 0,   /* zero + fixed-point CIC deposit                   */
-    COLAPM_PHASE_FFT_FWD,       /* x and y forward passes of the density            */
+    COLAPM_PHASE_DEPOSIT = 0,   /* fixed-point CIC deposit of a force computation   */
+    COLAPM_PHASE_FFT_FWD,       /* x and y forward passes of a force computation    */
     COLAPM_PHASE_POISSON,       /* z forward, Green/gradient/deconvolution, z inverse */
     COLAPM_PHASE_FFT_INV,       /* y inverse pass of the forces (both inverse passes
                                    with the fused x-y engine)                       */
     COLAPM_PHASE_GATHER,        /* CIC gather + kick + drift                        */
     COLAPM_PHASE_ICS,           /* initial conditions                               */
-    COLAPM_PHASE_POWER,         /* power-spectrum transform and binning             */
+    COLAPM_PHASE_POWER,         /* all of colapm_power: its deposit, forward passes,
+                                   z transform and binning                          */
     COLAPM_PHASE_FFT_INV_X,     /* x inverse pass of the three forces (c2r)         */
     COLAPM_PHASE_COUNT
 };
