@@ -99,7 +99,7 @@ __device__ __forceinline__ int sbin(int i, int L) { return i < L / 2 ? i : i - L
 // the rows of a z tile are 4 MB apart, every one in a different 2 MB page, which streams at about a
 // third of the bandwidth.
 template <int L, bool BLK>
-__device__ __forceinline__ size_t hs_index(int kx, int y, int z) {
+__host__ __device__ __forceinline__ size_t hs_index(int kx, int y, int z) {
     if constexpr (BLK)
         return ((((((size_t)(kx >> 3) * (L / 8) + (y >> 3)) * L + z) << 3) + (y & 7)) << 3) + (kx & 7);
     else return ((size_t)z * L + y) * (L / 2) + kx;
@@ -108,7 +108,7 @@ __device__ __forceinline__ size_t hs_index(int kx, int y, int z) {
 // Distance between rows y and y + d of one column when d and y are multiples of 8 apart from the
 // same residue (d a multiple of 8): what the passes add per register index.
 template <int L, bool BLK>
-__device__ __forceinline__ constexpr size_t hs_ystep(int d) {
+__host__ __device__ __forceinline__ constexpr size_t hs_ystep(int d) {
     return BLK ? (size_t)(d / 8) * L * 64 : (size_t)d * (L / 2);
 }
 
