@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(K2<L>::T) k2_fy(float2* __restrict__ data, siz
 // ---------------------------------------------------------------------------------------------
 // z pass with the spectral operator fused (see k_fz in fft_kernels.cuh for the algebra):
 // forward z (radices R1, R2) -> bases in registers -> inverse z (radices R2, R1) per base.
-// C columns per tile (8, or 4 to halve shared memory and fit two CTAs per SM).
+// C columns per tile: 8, or 4 (the blocked layout) to halve the shared memory per CTA.
 template <int L, int MODE, int C = 8, bool DIRECT = false>
 struct Z2 {
     static constexpr int R1 = F2<L>::R1, R2 = F2<L>::R2;

@@ -7,9 +7,10 @@ namespace colapm {
 template <int N, int MODE, bool BLK>
 static cudaError_t fz2(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm, PowerArgs pw,
                        cudaStream_t s) {
-    // Blocked layout: 4-column tiles (two CTAs per SM; 32-byte rows whose 512-byte runs the
-    // neighbouring tiles complete) measured 2% faster than 8-column ones, and 34% faster for the
-    // power spectrum. Standard layout: 8 columns (4-column rows there are 32 bytes 4 MB apart).
+    // Blocked layout: 4-column tiles (32-byte rows whose 512-byte runs the neighbouring tiles
+    // complete), which with the prefetch buffer measured 2% faster than 8-column ones (34% for the
+    // power spectrum), and with direct loads fit three CTAs per SM. Standard layout: 8 columns
+    // (4-column rows there are 32 bytes 4 MB apart).
     constexpr int CZ = BLK ? 4 : 8;
     constexpr bool DIRECT = BLK;   // blocked layout: loads straight into registers, three CTAs per SM
     using Z = Z2<N, MODE, CZ, DIRECT>;
