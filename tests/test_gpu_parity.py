@@ -259,6 +259,10 @@ def test_error_codes(C):
         with pytest.raises(C.ColapmError) as e:
             C.colapm_step(s.ctx, 1)                                # before ICs
         assert e.value.code == -6
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_get_particles_async(s.ctx, np.empty((16 ** 3, 3), np.float32), None)
+        assert e.value.code == -6
+        C.colapm_wait_particles(s.ctx)                             # nothing pending: returns at once
         C.colapm_make_ics(s.ctx)
         cell, off, _ = workloads.random_state(16, 32, 1)
         off[10, 1] = 1.0                                          # out of range
