@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--engine", default="default", choices=["default", "fused", "two_stage", "stockham"],
+                    help="FFT engine of the timed context (profiling aid; the default is the library's)")
     return ap.parse_args()
 
 
@@ -348,6 +350,9 @@ def main():
     np_, nm, nsteps = kw["np"], kw["nm"], kw["n_steps"]
     stream = torch.cuda.Stream()
     ctx = C.colapm_create(C.default_params(**kw), stream.cuda_stream)
+    if args.engine != "default":   # (fused x-y bits, two-stage) as colapm_set_engine takes them
+        fused, two = {"fused": (3, 1), "two_stage": (0, 1), "stockham": (0, 0)}[args.engine]
+        C.colapm_set_engine(ctx, fused, two, 256)
     nbins = 100
     kd = torch.empty(nbins, dtype=torch.float64, device="cuda")
     pd = torch.empty(nbins, dtype=torch.float64, device="cuda")
