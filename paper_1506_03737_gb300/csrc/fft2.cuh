@@ -37,7 +37,7 @@ template <int L, int RA, int LINES = 8>
 struct Xch {
     static constexpr int PITCH = L + L / RA + 4;   // = 4 (mod 16) for the sizes above
     static constexpr int SIZE = LINES * PITCH;     // float2 elements
-    __device__ __forceinline__ static int at(int c, int e) { return c * PITCH + e + e / RA; }
+    __host__ __device__ __forceinline__ static int at(int c, int e) { return c * PITCH + e + e / RA; }
 };
 
 // Twiddle tables for length L: w1[j] = w^j, w8[m][j] = w^(8 m j), w = exp(-2 pi i / L).
@@ -57,7 +57,7 @@ __device__ __forceinline__ void load_tw2(Tw2* t, const float2* __restrict__ g, i
 
 // Multiply v[r] by w^(S j r) for r < R (j < 32).
 template <int R, int S>
-__device__ __forceinline__ void twiddle2(float2* v, const Tw2* t, int j) {
+__host__ __device__ __forceinline__ void twiddle2(float2* v, const Tw2* t, int j) {
     float2 p[8];
     float2 w1 = t->w1[j];
     if (S > 0) w1 = cconj(w1);
@@ -115,7 +115,7 @@ __host__ __device__ __forceinline__ constexpr size_t hs_ystep(int d) {
 // Stage B of a line held in exchange buffer xb (stage-A radix RA), task j < RA of line c:
 // loads j + RA r, twiddles, RB-point DFT. Returns X[j + RA r] in v.
 template <int L, int RA, int RB, int S, int LINES = 8>
-__device__ __forceinline__ void stage_b(const float2* xb, const Tw2* tw, int c, int j, float2* v) {
+__host__ __device__ __forceinline__ void stage_b(const float2* xb, const Tw2* tw, int c, int j, float2* v) {
 #pragma unroll
     for (int r = 0; r < RB; ++r) v[r] = xb[Xch<L, RA, LINES>::at(c, j + RA * r)];
     twiddle2<RB, S>(v, tw, j);

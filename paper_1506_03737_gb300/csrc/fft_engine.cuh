@@ -35,16 +35,16 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 // multiply by s*i (s = +-1)
 template <int S>
-__device__ __forceinline__ float2 cmul_si(float2 a) { return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
+__host__ __device__ __forceinline__ float2 cmul_si(float2 a) { return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
 
 // cos and sin of 2 pi m / 32, m = 0..15 (mathematical constants rounded to float)
 #define COLAPM_C32(m) ((m) == 0 ? 1.0f : (m) == 1 ? 0.98078528040323044913f : (m) == 2 ? 0.92387953251128675613f : \
@@ -56,7 +56,7 @@ __device__ __forceinline__ float2 cmul_si(float2 a) { return S > 0 ? make_float2
 #define COLAPM_S32(m) ((m) == 0 ? 0.0f : COLAPM_C32(8 - (m) < 0 ? (m) - 8 : 8 - (m)))
 
 template <int R, int S>
-__device__ __forceinline__ float2 root(int k) {   // exp(S 2 pi i k / R), R in {2,4,8,16,32}, k < R/2 (unrolled)
+__host__ __device__ __forceinline__ float2 root(int k) {   // exp(S 2 pi i k / R), R in {2,4,8,16,32}, k < R/2 (unrolled)
     const int m = k * (32 / R);
     const float c = COLAPM_C32(m), s = COLAPM_S32(m);
     return make_float2(c, S > 0 ? s : -s);
@@ -64,7 +64,7 @@ __device__ __forceinline__ float2 root(int k) {   // exp(S 2 pi i k / R), R in {
 
 // In-register R-point DFT, X_k = sum_m v_m exp(S 2 pi i m k / R).
 template <int R, int S>
-__device__ __forceinline__ void dft(float2* v) {
+__host__ __device__ __forceinline__ void dft(float2* v) {
     if constexpr (R == 1) {
         return;
     } else if constexpr (R == 2) {
