@@ -169,6 +169,24 @@ def test_newtonian_limit_pair(sep):
     assert np.linalg.norm(f[0] - expect) < 0.03 * np.linalg.norm(expect)
 
 
+def test_force_and_lpt_spectra_vanish_on_the_nyquist_planes():
+    # Every spectral operator is zero on modes with any index at N/2 (the stencils stay odd and the
+    # fields real): the transforms of the force meshes and LPT displacements have no coefficient there.
+    nm = 16
+    rng = np.random.default_rng(12)
+    rho = pm.cic_deposit(rng.uniform(0, nm, size=(300, 3)), nm)
+    force = pm.force_mesh(pm.density_contrast(rho, 8, nm), BOX, 1)
+    _, _, _, nyq = ics.wavevectors(nm, BOX)
+    for j in range(3):
+        fk = fft.fftn(force[j])
+        assert np.abs(fk[nyq]).max() < 1e-12 * np.abs(fk).max(), j
+    dk = ics.gaussian_field(nm, BOX, 3, cosmology.linear_pk(0.3, 0.7, 0.96, 0.8))
+    for field in ics.lpt_displacements(dk, BOX):
+        for j in range(3):
+            fk = fft.fftn(field[j])
+            assert np.abs(fk[nyq]).max() < 1e-12 * np.abs(fk).max(), j
+
+
 def test_mesh_force_of_a_sinusoid_is_exact():
     nm, amp = 16, 0.1
     k1 = 2 * math.pi / BOX
@@ -182,10 +200,41 @@ def test_mesh_force_of_a_sinusoid_is_exact():
     assert np.abs(force1[0] * w - force[0]).max() < 1e-12 * amp / k1
 
 
+def test_uniform_lattice_has_zero_contrast_at_mesh_ratio_two():
+    # The Lagrangian lattice sits half a PM cell off the mesh nodes. With N_m = 2 N_p each particle
+    # splits equally over 8 cells and every cell receives exactly 1/8 of one particle, so the mass
+    # per cell times the particle mass (N_m/N_p)^3 = 8 cells is exactly the mean: delta = 0 everywhere.
+    for np_, nm in ((8, 16), (4, 4)):
+        q = ics.lagrangian_grid(np_, BOX, nm)
+        rho = pm.cic_deposit(q * (nm / BOX), nm)
+        assert np.all(rho == rho.flat[0]) and rho.sum() == np_ ** 3 << 45
+        assert np.abs(pm.density_contrast(rho, np_, nm)).max() == 0.0
+    # Any positions: the contrast averages to zero (mass conservation with the particle mass above).
+    rng = np.random.default_rng(9)
+    u = rng.uniform(0, 16, size=(8 ** 3, 3))
+    assert abs(pm.density_contrast(pm.cic_deposit(u, 16), 8, 16).mean()) < 1e-15
+
+
+@pytest.mark.parametrize("sep", [5.0, 7.0])
+def test_newtonian_limit_pair_at_mesh_ratio_two(sep):
+    # With N_m = 2 N_p one particle carries (N_m/N_p)^3 = 8 cell volumes of mass: the pair force far
+    # from the mesh scale approaches -8 r_hat / (4 pi r^2) in cell units (Gauss's law).
+    nm = 64
+    box = float(nm)
+    d = np.array([0.3, 1.0, 0.6])
+    d /= np.linalg.norm(d)
+    x = np.array([[30.6, 12.2, 40.9], [0, 0, 0]])
+    x[1] = x[0] + sep * d
+    f, _ = pm.pm_accel(x, box, nm // 2, nm)
+    expect = 8.0 * sep ** -2 / (4 * math.pi) * d
+    assert np.linalg.norm(f[0] - expect) < 0.03 * np.linalg.norm(expect)
+    assert np.linalg.norm(f[1] + expect) < 0.03 * np.linalg.norm(expect)
+
+
 # --- COLA / PM stepping (§2.3) -------------------------------------------------------------
 
-def pancake_error(np_, nm, n_steps, cola_on, stepping="modified", amp=0.5):
-    r = cola.Run(BOX, np_, nm, 0.3, 9.0, 0.0, n_steps, stepping=stepping, cola=cola_on)
+def pancake_error(np_, nm, n_steps, cola_on, stepping="modified", amp=0.5, deconv=1):
+    r = cola.Run(BOX, np_, nm, 0.3, 9.0, 0.0, n_steps, stepping=stepping, cola=cola_on, deconv=deconv)
     a = amp / r.table["D1"][-1]
     r.set_displacements(*ics.lpt_displacements(plane_wave_field(np_, [((1, 0, 0), a)]), BOX))
     if cola_on:
@@ -199,6 +248,132 @@ def test_pancake_cola_ten_steps():
     # 1-D Zel'dovich solution is exact before shell crossing; the remaining error is the PM
     # discreteness of 32 sheets (measured 9.8e-3 at 32^3, 3.8e-3 at 64^3).
     assert pancake_error(32, 32, 10, True) < 1.5e-2
+
+
+def test_pancake_cola_at_mesh_ratio_two():
+    # N_m = 2 N_p, the ratio of the benchmarked runs: the mass normalisation (N_m/N_p)^3 enters the
+    # force. Without the CIC deconvolution the 32 displaced sheets are followed to 1.9e-2 rms; with it
+    # (the default) the sheets' own graininess near the mesh Nyquist frequency is amplified by 1/W:
+    # 4.8e-2 measured, 2.7e-2 at 64 sheets on a 128 mesh (PM discreteness, converging).
+    assert pancake_error(32, 64, 10, True, deconv=0) < 2.5e-2
+    assert pancake_error(32, 64, 10, True) < 6e-2
+
+
+def test_finalize_total_momentum_of_the_pancake():
+    # Before shell crossing the exact 1-D solution is x = q + D1 Psi1, so the total momentum
+    # p = a^3 E dx/da at a_N is P1(a_N) Psi1 (Psi2 = 0): finalize must return it, to the PM
+    # discreteness of the positions (1.0e-2 measured at 32 sheets).
+    amp = 0.5
+    r = cola.Run(BOX, 32, 32, 0.3, 9.0, 0.0, 10)
+    a = amp / r.table["D1"][-1]
+    r.set_displacements(*ics.lpt_displacements(plane_wave_field(32, [((1, 0, 0), a)]), BOX))
+    r.run()
+    p = r.finalize()
+    exact = r.table["P1"][-1] * r.psi1
+    assert np.sqrt(np.mean((p - exact) ** 2)) < 1.5e-2 * np.abs(exact).max()
+    assert np.abs(p[:, 1:]).max() < 1e-12 * np.abs(exact).max()
+
+
+def test_finalize_adds_the_lpt_frame_momentum():
+    # COLA moves particles as x = x_res + D1(a) Psi1 + D2(a) Psi2 (§2.3), so the total momentum
+    # p = a^3 E dx/da is the residual one plus a^3 E (dD1/da Psi1 + dD2/da Psi2). The derivatives
+    # are taken here by central differences of the growth factors (pinned by the EdS closed forms
+    # and the Heath integral), not from the momenta P1, P2 that finalize uses.
+    om, box, np_ = 0.3, 64.0, 8
+    rng = np.random.default_rng(17)
+    r = cola.Run(box, np_, 16, om, 9.0, 0.5, 4)
+    r.set_displacements(rng.standard_normal((3, np_, np_, np_)), 0.6 * rng.standard_normal((3, np_, np_, np_)))
+    r.run()
+    p_total = r.finalize()
+    a, h = r.table["a"][-1], 1e-3
+    d1p, d2p, _, _ = cosmology.growth(np.array([a + h]), om)
+    d1m, d2m, _, _ = cosmology.growth(np.array([a - h]), om)
+    a3e = a ** 3 * cosmology.hubble_e(a, om)
+    expect = a3e * ((d1p - d1m) / (2 * h) * r.psi1 + (d2p - d2m) / (2 * h) * r.psi2)
+    assert np.abs(p_total - r.p - expect).max() < 1e-5 * np.abs(expect).max()
+
+
+def lpt_acceleration_coefficients(a, om):
+    """(c1, c2) per scale factor a (array), with the acceleration of the exact LPT trajectory
+    x = q + D1 Psi1 + D2 Psi2 equal to c1 Psi1 + c2 Psi2 in the force units of the kick: the equation
+    of motion dp/da = 1.5 Om F / (a^2 E) with p = a^3 E dx/da (§2.3) gives
+    F = a^2 E / (1.5 Om) d/da [a^3 E dD/da] per LPT order. The two derivatives are nested central
+    differences of the growth factors alone."""
+    a = np.asarray(a, dtype=np.float64)
+    h = 2e-3 * a
+    d1, d2, _, _ = cosmology.growth(np.concatenate([a - 2 * h, a, a + 2 * h]), om)
+    e = cosmology.hubble_e
+
+    def outer(d):
+        d = d.reshape(3, -1)
+        lo = (a - h) ** 3 * e(a - h, om) * (d[1] - d[0]) / (2 * h)
+        hi = (a + h) ** 3 * e(a + h, om) * (d[2] - d[1]) / (2 * h)
+        return a * a * e(a, om) / (1.5 * om) * (hi - lo) / (2 * h)
+    return outer(d1), outer(d2)
+
+
+class LptForceRun(cola.Run):
+    """A run whose force is the acceleration of the exact LPT trajectory at the current a_i."""
+
+    def force(self):
+        if not hasattr(self, "_coef"):
+            self._coef = lpt_acceleration_coefficients(self.table["a"], self.om)
+        i = self.step_index
+        return self._coef[0][i] * self.psi1 + self._coef[1][i] * self.psi2
+
+
+def lpt_momentum(r):
+    """a^3 E dx/da of the exact LPT trajectory at a_N, by central differences of the growth factors."""
+    a, om = r.table["a"][-1], r.om
+    h = 2e-3 * a
+    d1p, d2p, _, _ = cosmology.growth(np.array([a + h]), om)
+    d1m, d2m, _, _ = cosmology.growth(np.array([a - h]), om)
+    return a ** 3 * cosmology.hubble_e(a, om) * ((d1p - d1m) / (2 * h) * r.psi1 + (d2p - d2m) / (2 * h) * r.psi2)
+
+
+def lpt_trajectory_run(cola_on, n_steps, spacing="lin", stepping="modified", finalize=False):
+    """Relative max error of the positions at a_N (and, with finalize, of the final momenta)."""
+    om, box, np_ = 0.3, 64.0, 4
+    rng = np.random.default_rng(23)
+    r = LptForceRun(box, np_, 8, om, 9.0, 0.0, n_steps, spacing=spacing, stepping=stepping, cola=cola_on)
+    r.set_displacements(rng.standard_normal((3, np_, np_, np_)), rng.standard_normal((3, np_, np_, np_)))
+    r.run()
+    t = r.table
+    exact = t["D1"][-1] * r.psi1 + t["D2"][-1] * r.psi2
+    err = np.abs(r.displacement() - exact).max() / np.abs(exact).max()
+    if not finalize:
+        return r, err
+    p_exact = lpt_momentum(r)
+    return r, err, np.abs(r.finalize() - p_exact).max() / np.abs(p_exact).max()
+
+
+@pytest.mark.parametrize("stepping", ["modified", "quinn"])
+def test_cola_follows_the_exact_lpt_trajectory(stepping):
+    # Given the exact acceleration of the 2LPT trajectory (Psi2 != 0), COLA's residual force is zero
+    # (the LPT terms of the kick are what the growth equations make of the two modes), so the residual
+    # momentum stays zero, the particles stay on x = q + D1 Psi1 + D2 Psi2 after any number of steps,
+    # and finalize returns p = a^3 E dx/da at a_N (derivatives by central differences, not P1, P2).
+    r, err = lpt_trajectory_run(True, 10, stepping=stepping)
+    assert err < 1e-5
+    assert np.abs(r.p).max() < 1e-5 * np.abs(r.psi1).max()
+    p_total = r.finalize()
+    assert np.abs(r.p).max() < 1e-5 * np.abs(r.psi1).max()
+    expect = lpt_momentum(r)
+    assert np.abs(p_total - expect).max() < 1e-5 * np.abs(expect).max()
+
+
+def test_plain_pm_converges_to_the_exact_lpt_trajectory():
+    # COLA off (§7.1): the same exact acceleration, integrated by the kick and drift coefficients alone
+    # from the 2LPT momentum, converges to the LPT trajectory as the steps shrink (leapfrog: second
+    # order in the step), for linear and logarithmic spacing in a.
+    # The closing half kick of finalize synchronises the momentum with the positions at a_N, so the
+    # final momentum converges at second order as well.
+    for spacing, stepping in itertools.product(("lin", "log"), ("modified", "quinn")):
+        runs = [lpt_trajectory_run(False, n, spacing, stepping, finalize=True) for n in (20, 40, 80)]
+        for k in (1, 2):
+            errs = [run[k] for run in runs]
+            assert errs[2] < errs[1] < errs[0] < 2e-2, (spacing, stepping, k, errs)
+            assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0, (spacing, stepping, k, errs)
 
 
 def test_pancake_plain_pm_converges():
@@ -260,6 +435,29 @@ def test_power_single_mode_and_cross_correlation():
     assert abs(r[b[0]] - 1) < 1e-12
     r = power.cross_correlation(dk, -dk, BOX, 20, kf, kf * n / 2)
     assert abs(r[b[0]] + 1) < 1e-12
+
+
+def test_power_cic_window_of_a_planted_mode():
+    # One planted mode n = (3, -2, 5) with all three indices non-zero (and its conjugate): the
+    # windowed estimator must give L^3 (A/2)^2 / W(n)^2 with W = prod_i sinc^2(pi n_i / N) (§7.1),
+    # the CIC window divided out twice in power (once per delta_k).
+    n, amp = 16, 0.1
+    m = (3, -2, 5)
+    dk = plane_wave_field(n, [(m, amp)])
+    kf = 2 * math.pi / BOX
+    w = 1.0
+    for mi in m:
+        x = math.pi * mi / n
+        w *= (math.sin(x) / x) ** 2
+    kmean, pb, cnt = power.binned_power(dk, BOX, 20, kf, kf * n / 2, window=True)
+    b = np.flatnonzero(cnt > 0)
+    sel = b[np.nan_to_num(pb[b]) > 0]
+    assert len(sel) == 1
+    i = sel[0]
+    assert abs(pb[i] * cnt[i] / 2 / (BOX ** 3 * (amp / 2) ** 2 / w ** 2) - 1) < 1e-12
+    # and without the window the bare |delta_k|^2 normalisation
+    _, pb0, _ = power.binned_power(dk, BOX, 20, kf, kf * n / 2, window=False)
+    assert abs(pb0[i] * cnt[i] / 2 / (BOX ** 3 * (amp / 2) ** 2) - 1) < 1e-12
 
 
 def test_planar_force_reduces_the_3d_operator_to_one_axis():

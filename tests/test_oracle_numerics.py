@@ -117,6 +117,8 @@ def test_quinn_coefficients_eds():
     drift = 2.0 * (a[:-1] ** -0.5 - a[1:] ** -0.5)
     assert np.abs(t["kick"] / kick - 1).max() < 1e-11
     assert np.abs(t["drift"] / drift - 1).max() < 1e-11
+    # the closing half kick of finalize covers [a_{N-1/2}, a_N]
+    assert abs(t["kick_final"] / (1.5 * 2.0 * (math.sqrt(a[-1]) - math.sqrt(ah[-1]))) - 1) < 1e-11
 
 
 def test_modified_coefficients_eds():
@@ -128,6 +130,18 @@ def test_modified_coefficients_eds():
     # int a^(n-3) / E da = int a^(n - 3/2) da in EdS.
     drift = ah ** -n * (a[1:] ** (n - 0.5) - a[:-1] ** (n - 0.5)) / (n - 0.5)
     assert np.abs(t["kick"] / kick - 1).max() < 1e-11
+    assert np.abs(t["drift"] / drift - 1).max() < 1e-11
+
+
+def test_log_spacing_is_geometric_in_a():
+    # §7.3: steps logarithmic in a. From z = 9 to 0 in 10 steps a_i = 10^((i - 10) / 10).
+    a = cosmology.scale_factors(9.0, 0.0, 10, "log")
+    assert np.abs(a / 10.0 ** ((np.arange(11) - 10) / 10.0) - 1).max() < 1e-14
+    lin = cosmology.scale_factors(9.0, 0.0, 10, "lin")
+    assert np.abs(lin - (0.1 + 0.09 * np.arange(11))).max() < 1e-15
+    # the table follows the spacing it is given: EdS Quinn drift over each geometric step
+    t = cosmology.timestep_table(1.0, 9.0, 0.0, 10, spacing="log", stepping="quinn")
+    drift = 2.0 * (a[:-1] ** -0.5 - a[1:] ** -0.5)
     assert np.abs(t["drift"] / drift - 1).max() < 1e-11
 
 
