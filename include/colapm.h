@@ -253,20 +253,23 @@ void colapm_batch_destroy(colapm_batch* b);
  * and so cannot create a context. It computes what colapm_power computes (same deposit,
  * transform, binning and FP64 sums) for `n_particles` positions given as integer mesh cells
  * (`cell`, xyz int32, each in [0, nm)) and offsets (`offset`, xyz float, each in [0, 1)), both
- * DEVICE arrays owned by the caller; the mean density is n_particles / nm^3 per cell. Outputs
- * (nbins each, host or device): mean |k|, mean P, mode count. kmin <= 0 selects 2 pi / box,
- * kmax <= 0 selects pi nm / box.
+ * DEVICE arrays of the current device (or managed memory), owned by the caller; the mean density
+ * is n_particles / nm^3 per cell. Outputs (nbins each, host or device): mean |k|, mean P, mode
+ * count. kmin <= 0 selects 2 pi / box, kmax <= 0 selects pi nm / box. A cell whose fixed-point
+ * mass reaches 2^63 (2^18 particles) returns COLAPM_E_OVERFLOW.
  *
  * All working memory lives in one fixed device array inside the library, sized for
  * nm <= COLAPM_NOALLOC_MAX_NM (one of 16, 32, 64, 96, 128) and nbins <= COLAPM_NOALLOC_MAX_BINS;
- * larger sizes, host input arrays or positions out of range return COLAPM_E_ARG. Every GPU
+ * larger sizes, host input arrays, arrays on another GPU or positions out of range return
+ * COLAPM_E_ARG. Every GPU
  * that loads the library holds that array (about 25 MB) until the process exits. The call
  * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). Every call
  * shares the array and leaves the last call's contents in it; each call clears what must
  * start at zero. Calls that overlap on the GPU (e.g. on two unordered streams) race on the
  * array and must not be issued. The first call on a device looks up the array's device
  * address for that device (once) and should come before any stream capture. Work runs on
- * `stream` (a cudaStream_t, may be NULL); the call synchronises that stream before returning. */
+ * `stream` (a cudaStream_t, may be NULL); the call synchronises that stream before returning,
+ * also when it fails after queueing work. */
 #define COLAPM_NOALLOC_MAX_NM 128
 #define COLAPM_NOALLOC_MAX_BINS 512
 int colapm_power_noalloc(const int* cell, const float* offset, long long n_particles, int nm, double box,

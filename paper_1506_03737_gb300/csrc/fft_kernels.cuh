@@ -23,6 +23,7 @@
 
 #include "colapm_internal.h"
 #include "fft_engine.cuh"
+#include "launch_cache.h"
 
 namespace colapm {
 
@@ -107,22 +108,6 @@ __device__ __forceinline__ void tile_to_rows(const float2* tile, float2* stg, fl
     }
 }
 
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// Persistent grid: resident CTAs per SM x SMs.
-template <typename K>
-static int persistent_grid(K kernel, int threads, size_t smem) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
-    if (per < 1) per = 1;
-    return per * sms;
-}
 
 // ---------------------------------------------------------------------------------------------
 // x passes: threads per CTA (the stages use n/2 of them; the copies and transposes all).

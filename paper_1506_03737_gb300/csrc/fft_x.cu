@@ -8,12 +8,10 @@ template <int n, bool I64, bool BLK>
 static cudaError_t fx_fwd2(const void* in, float2* out, const float2* tw, float scale, int* err, cudaStream_t s,
                            unsigned long long* zero) {
     using X = X2<n>;
-    static int grid2 = 0;
-    if (!grid2) {
-        cudaError_t e = set_smem(k2_fx_fwd<n, I64, BLK>, X::SMEM);
-        if (e != cudaSuccess) return e;
-        grid2 = persistent_grid(k2_fx_fwd<n, I64, BLK>, X::T, X::SMEM);
-    }
+    static GridCache cache;
+    int grid2 = 0;
+    cudaError_t e = cached_grid(cache, k2_fx_fwd<n, I64, BLK>, X::T, X::SMEM, &grid2);
+    if (e != cudaSuccess) return e;
     const int items = 2 * n * 2 * n / 8;
     k2_fx_fwd<n, I64, BLK><<<grid2 < items ? grid2 : items, X::T, X::SMEM, s>>>(in, out, tw, scale, err, items, zero);
     return cudaGetLastError();
@@ -29,12 +27,10 @@ static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float
     }
     if (blocked) return cudaErrorInvalidValue;
     using C = FxFwd<n, I64>;
-    static int grid = 0;
-    if (!grid) {
-        cudaError_t e = set_smem(k_fx_fwd<n, I64>, C::SMEM);
-        if (e != cudaSuccess) return e;
-        grid = persistent_grid(k_fx_fwd<n, I64>, C::T, C::SMEM);
-    }
+    static GridCache cache;
+    int grid = 0;
+    cudaError_t e = cached_grid(cache, k_fx_fwd<n, I64>, C::T, C::SMEM, &grid);
+    if (e != cudaSuccess) return e;
     const int items = N * N / 8;
     k_fx_fwd<n, I64><<<grid < items ? grid : items, C::T, C::SMEM, s>>>(in, out, tw, scale, err, items, zero);
     return cudaGetLastError();
@@ -43,12 +39,10 @@ static cudaError_t fx_fwd_t(const void* in, float2* out, const float2* tw, float
 template <int n, bool BLK>
 static cudaError_t fx_inv2(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s, float2* dst) {
     using X = X2<n>;
-    static int grid2 = 0;
-    if (!grid2) {
-        cudaError_t e = set_smem(k2_fx_inv<n, BLK>, X::SMEM_INV);
-        if (e != cudaSuccess) return e;
-        grid2 = persistent_grid(k2_fx_inv<n, BLK>, X::T, X::SMEM_INV);
-    }
+    static GridCache cache;
+    int grid2 = 0;
+    cudaError_t e = cached_grid(cache, k2_fx_inv<n, BLK>, X::T, X::SMEM_INV, &grid2);
+    if (e != cudaSuccess) return e;
     const int ipf = 2 * n * 2 * n / 8, items = ipf * nfields;
     k2_fx_inv<n, BLK><<<grid2 < items ? grid2 : items, X::T, X::SMEM_INV, s>>>(data, fstride, tw, ipf, nfields, dst);
     return cudaGetLastError();
@@ -64,12 +58,10 @@ static cudaError_t fx_inv_t(float2* data, size_t fstride, int nfields, const flo
     }
     if (blocked || (dst && dst != data)) return cudaErrorInvalidValue;
     using C = FxInv<n>;
-    static int grid = 0;
-    if (!grid) {
-        cudaError_t e = set_smem(k_fx_inv<n>, C::SMEM);
-        if (e != cudaSuccess) return e;
-        grid = persistent_grid(k_fx_inv<n>, C::T, C::SMEM);
-    }
+    static GridCache cache;
+    int grid = 0;
+    cudaError_t e = cached_grid(cache, k_fx_inv<n>, C::T, C::SMEM, &grid);
+    if (e != cudaSuccess) return e;
     const int ipf = N * N / 8, items = ipf * nfields;
     k_fx_inv<n><<<grid < items ? grid : items, C::T, C::SMEM, s>>>(data, fstride, tw, ipf, nfields);
     return cudaGetLastError();

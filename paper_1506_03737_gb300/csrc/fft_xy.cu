@@ -24,6 +24,7 @@
 // runs; it holds both, and finishes the current item (whose waits are on smaller tickets) first. Ring data uses default stores so it stays in L2; the input
 // planes are read and the final planes written with the streaming (.cs) policy.
 #include "fft2.cuh"
+#include "launch_cache.h"
 
 namespace colapm {
 
@@ -345,20 +346,7 @@ __global__ void __launch_bounds__(XY_T, 2) k_xy_fwd(const unsigned long long* __
     if (over) atomicOr(err, 1);
 }
 
-// Persistent grid: resident CTAs per SM x SMs, with the kernel's shared-memory attribute set once.
-int xy_grid(const void* fn, size_t smem, int* cache) {
-    if (!*cache) {
-        int dev = 0, sms = 0, occ = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, XY_T, smem);
-        *cache = sms * (occ > 0 ? occ : 1);
-    }
-    return *cache;
-}
-
-int g_fwd512, g_fwd1024, g_inv512, g_inv1024;
+GridCache g_fwd512, g_fwd1024, g_inv512, g_inv1024;   // per-device persistent grids
 
 }  // namespace
 
@@ -372,13 +360,16 @@ cudaError_t launch_xy_fwd(int nm, const unsigned long long* rho, float2* out, co
                           float2* ring, int* ctr, int* err, cudaStream_t s, bool zero_input) {
     cudaError_t e = cudaMemsetAsync(ctr, 0, xy_ctr_ints(nm, 1) * sizeof(int), s);
     if (e) return e;
+    int grid = 0;
     switch (nm) {
     case 512:
-        k_xy_fwd<512><<<xy_grid((const void*)k_xy_fwd<512>, XY<512>::SMEM, &g_fwd512), XY_T, XY<512>::SMEM, s>>>(
+        if ((e = cached_grid(g_fwd512, k_xy_fwd<512>, XY_T, XY<512>::SMEM, &grid)) != cudaSuccess) return e;
+        k_xy_fwd<512><<<grid, XY_T, XY<512>::SMEM, s>>>(
             rho, out, tw, scale, ring, ctr, err, zero_input);
         break;
     case 1024:
-        k_xy_fwd<1024><<<xy_grid((const void*)k_xy_fwd<1024>, XY<1024>::SMEM, &g_fwd1024), XY_T, XY<1024>::SMEM, s>>>(
+        if ((e = cached_grid(g_fwd1024, k_xy_fwd<1024>, XY_T, XY<1024>::SMEM, &grid)) != cudaSuccess) return e;
+        k_xy_fwd<1024><<<grid, XY_T, XY<1024>::SMEM, s>>>(
             rho, out, tw, scale, ring, ctr, err, zero_input);
         break;
     default: return cudaErrorInvalidValue;
@@ -391,13 +382,16 @@ cudaError_t launch_xy_inv(int nm, float2* data, size_t fstride, int nfields, con
     if (nfields < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(ctr, 0, xy_ctr_ints(nm, nfields) * sizeof(int), s);
     if (e) return e;
+    int grid = 0;
     switch (nm) {
     case 512:
-        k_xy_inv<512><<<xy_grid((const void*)k_xy_inv<512>, XY<512>::SMEM, &g_inv512), XY_T, XY<512>::SMEM, s>>>(
+        if ((e = cached_grid(g_inv512, k_xy_inv<512>, XY_T, XY<512>::SMEM, &grid)) != cudaSuccess) return e;
+        k_xy_inv<512><<<grid, XY_T, XY<512>::SMEM, s>>>(
             data, fstride, nfields, tw, ring, ctr, err);
         break;
     case 1024:
-        k_xy_inv<1024><<<xy_grid((const void*)k_xy_inv<1024>, XY<1024>::SMEM, &g_inv1024), XY_T, XY<1024>::SMEM, s>>>(
+        if ((e = cached_grid(g_inv1024, k_xy_inv<1024>, XY_T, XY<1024>::SMEM, &grid)) != cudaSuccess) return e;
+        k_xy_inv<1024><<<grid, XY_T, XY<1024>::SMEM, s>>>(
             data, fstride, nfields, tw, ring, ctr, err);
         break;
     default: return cudaErrorInvalidValue;

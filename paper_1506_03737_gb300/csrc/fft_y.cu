@@ -8,12 +8,10 @@ template <int N, int S, bool BLK>
 static cudaError_t fy2(float2* data, size_t fstride, int nfields, const float2* tw, cudaStream_t s) {
     using K = K2<N>;
     constexpr size_t smem = sizeof(float2) * Xch<N, K::RA>::SIZE + sizeof(Tw2);
-    static int grid2 = 0;
-    if (!grid2) {
-        cudaError_t e = set_smem(k2_fy<N, S, BLK>, smem);
-        if (e != cudaSuccess) return e;
-        grid2 = persistent_grid(k2_fy<N, S, BLK>, K::T, smem);
-    }
+    static GridCache cache;
+    int grid2 = 0;
+    cudaError_t e = cached_grid(cache, k2_fy<N, S, BLK>, K::T, smem, &grid2);
+    if (e != cudaSuccess) return e;
     const int total = (N / 2 / 8) * N * nfields;
     k2_fy<N, S, BLK><<<grid2 < total ? grid2 : total, K::T, smem, s>>>(data, fstride, tw, nfields);
     return cudaGetLastError();
@@ -28,12 +26,10 @@ static cudaError_t fy_sign(float2* data, size_t fstride, int nfields, const floa
     if (blocked) return cudaErrorInvalidValue;
     using C = Fy<N>;
     constexpr size_t smem = C::SMEM;
-    static int grid = 0;
-    if (!grid) {
-        cudaError_t e = set_smem(k_fy<N, S>, smem);
-        if (e != cudaSuccess) return e;
-        grid = persistent_grid(k_fy<N, S>, C::T, smem);
-    }
+    static GridCache cache;
+    int grid = 0;
+    cudaError_t e = cached_grid(cache, k_fy<N, S>, C::T, smem, &grid);
+    if (e != cudaSuccess) return e;
     const int total = (N / 2 / 8) * N * nfields;
     k_fy<N, S><<<grid < total ? grid : total, C::T, smem, s>>>(data, fstride, tw, nfields);
     return cudaGetLastError();
@@ -50,12 +46,10 @@ template <int N>
 static cudaError_t fy_force_t(float2* data, size_t fstride, const float2* tw, cudaStream_t s) {
     using K = K2<N>;
     constexpr size_t smem = sizeof(float2) * Xch<N, K::RA>::SIZE + sizeof(Tw2);
-    static int grid = 0;
-    if (!grid) {
-        cudaError_t e = set_smem(k2_fy_force<N>, smem);
-        if (e != cudaSuccess) return e;
-        grid = persistent_grid(k2_fy_force<N>, K::T, smem);
-    }
+    static GridCache cache;
+    int grid = 0;
+    cudaError_t e = cached_grid(cache, k2_fy_force<N>, K::T, smem, &grid);
+    if (e != cudaSuccess) return e;
     const int total = (N / 2 / 8) * N;
     k2_fy_force<N><<<grid < total ? grid : total, K::T, smem, s>>>(data, fstride, tw);
     return cudaGetLastError();

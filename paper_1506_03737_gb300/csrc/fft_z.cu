@@ -15,14 +15,10 @@ static cudaError_t fz2(float2* in, ZOut out, const float2* tw, const float* sinc
     constexpr bool DIRECT = BLK;   // blocked layout: loads straight into registers, three CTAs per SM
     using Z = Z2<N, MODE, CZ, DIRECT>;
     const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
-    static size_t configured2 = 0;
-    static int grid2 = 0;
-    if (smem > configured2 || !grid2) {
-        cudaError_t e = set_smem(k2_fz<N, MODE, CZ, BLK, DIRECT>, smem);
-        if (e != cudaSuccess) return e;
-        configured2 = smem > configured2 ? smem : configured2;
-        grid2 = persistent_grid(k2_fz<N, MODE, CZ, BLK, DIRECT>, Z::T, smem);
-    }
+    static GridCache cache;
+    int grid2 = 0;
+    cudaError_t e = cached_grid(cache, k2_fz<N, MODE, CZ, BLK, DIRECT>, Z::T, smem, &grid2);
+    if (e != cudaSuccess) return e;
     const int total = (N / 2 / CZ) * N;
     k2_fz<N, MODE, CZ, BLK, DIRECT><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
     return cudaGetLastError();
@@ -42,14 +38,10 @@ static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* 
     if (blocked) return cudaErrorInvalidValue;
     using C = Fz<N, MODE>;
     const size_t smem = C::BASE_SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
-    static size_t configured = 0;
-    static int grid = 0;
-    if (smem > configured || !grid) {
-        cudaError_t e = set_smem(k_fz<N, MODE>, smem);
-        if (e != cudaSuccess) return e;
-        configured = smem > configured ? smem : configured;
-        grid = persistent_grid(k_fz<N, MODE>, C::T, smem);
-    }
+    static GridCache cache;
+    int grid = 0;
+    cudaError_t e = cached_grid(cache, k_fz<N, MODE>, C::T, smem, &grid);
+    if (e != cudaSuccess) return e;
     const int total = (N / 2 / 8) * N;
     k_fz<N, MODE><<<grid < total ? grid : total, C::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
     return cudaGetLastError();

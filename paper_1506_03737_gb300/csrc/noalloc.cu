@@ -64,7 +64,10 @@ __global__ void k_deposit_xyz(const int* __restrict__ cell, const float* __restr
                 const unsigned long long wt = w[0][dx] * w[1][dy] * w[2][dz];
                 if (!wt) continue;
                 const int x = (c[0] + dx) % nm, y = (c[1] + dy) % nm, z = (c[2] + dz) % nm;
-                atomicAdd(rho + ((size_t)z * nm + y) * nm + x, wt);
+                // n_particles has no upper bound here, so a cell could wrap past 2^64 and come back
+                // below 2^63 unseen by the transform's top-bit check: flag it from the old value.
+                const unsigned long long old = atomicAdd(rho + ((size_t)z * nm + y) * nm + x, wt);
+                if (old + wt < old || old + wt >= (1ull << 63)) atomicOr(err, 1);
             }
 }
 
@@ -96,13 +99,16 @@ __global__ void k_finish(const double* __restrict__ acc, int nbins, double* __re
 std::mutex g_mu;
 unsigned char* g_dev_ptr[64] = {};
 
-bool device_resident(const void* p) {
+// Device memory of the current device `dev` (memory of another GPU is rejected: without peer
+// access the kernels could not read it), or managed memory.
+bool device_resident(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -118,15 +124,14 @@ extern "C" int colapm_power_noalloc(const int* cell, const float* offset, long l
     for (int s : sizes) ok_nm |= (s == nm);
     if (!ok_nm || nm > kMaxNm || nbins < 1 || nbins > kMaxBins || n_particles < 1 || !(box > 0)) return COLAPM_E_ARG;
     if (!cell || !offset || !k_out || !p_out || !nmodes_out) return COLAPM_E_ARG;
-    if (!device_resident(cell) || !device_resident(offset)) return COLAPM_E_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return COLAPM_E_CUDA;
+    if (!device_resident(cell, dev) || !device_resident(offset, dev)) return COLAPM_E_ARG;
     const double kf = 2.0 * M_PI / box;
     if (kmin <= 0) kmin = kf;
     if (kmax <= 0) kmax = M_PI * nm / box;
     if (!(kmax > kmin)) return COLAPM_E_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return COLAPM_E_CUDA;
     unsigned char* base;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -163,9 +168,14 @@ extern "C" int colapm_power_noalloc(const int* cell, const float* offset, long l
     const int n2max = 3 * (nm / 2) * (nm / 2);
     const size_t nm3 = (size_t)nm * nm * nm;
 
+    // Once work is queued, an error return first waits (best effort) for what was queued, so that no
+    // kernel of this call still writes the shared array when the caller retries, even on another stream.
 #define NCK(x)                                  \
     do {                                        \
-        if ((x) != cudaSuccess) return COLAPM_E_CUDA; \
+        if ((x) != cudaSuccess) {               \
+            cudaStreamSynchronize(s);           \
+            return COLAPM_E_CUDA;               \
+        }                                       \
     } while (0)
     NCK(cudaMemcpyAsync(tw, h_tw, sizeof(float2) * nm, cudaMemcpyHostToDevice, s));
     NCK(cudaMemcpyAsync(sinc2, h_s2, sizeof(float) * nm, cudaMemcpyHostToDevice, s));

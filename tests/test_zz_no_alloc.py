@@ -58,3 +58,32 @@ def test_noalloc_rejects_oversize_and_host_inputs(C):
     with pytest.raises(C.ColapmError) as e:
         C.colapm_power_noalloc(cell.cpu().numpy(), off.cpu().numpy(), 8, 64, 100.0, 10)   # host inputs
     assert e.value.code == -1
+
+
+def test_noalloc_rejects_arrays_on_another_gpu(C):
+    # The call runs on the current device; positions held by another GPU are refused on the host,
+    # before anything is queued.
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs a second GPU")
+    cell = torch.zeros((8, 3), dtype=torch.int32, device="cuda:1")
+    off = torch.zeros((8, 3), dtype=torch.float32, device="cuda:1")
+    torch.cuda.set_device(0)
+    with pytest.raises(C.ColapmError) as e:
+        C.colapm_power_noalloc(cell, off, 8, 64, 100.0, 10)
+    assert e.value.code == -1
+
+
+def test_noalloc_reports_a_full_cell(C):
+    # 2^18 particles on one node put 2^63 into one cell of the fixed-point mesh: an overflow the
+    # deposit itself reports, whatever the particle count.
+    import torch
+    n = 1 << 18
+    cell = torch.zeros((n, 3), dtype=torch.int32, device="cuda")
+    off = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(C.ColapmError) as e:
+        C.colapm_power_noalloc(cell, off, n, 16, 100.0, 10)
+    assert e.value.code == -4
+    # the next call clears the shared array and succeeds
+    k, p, cnt = C.colapm_power_noalloc(cell[:8], off[:8], 8, 16, 100.0, 10)
+    assert cnt.sum() > 0
