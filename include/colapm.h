@@ -119,6 +119,18 @@ int colapm_finalize(colapm_ctx* ctx);
 int colapm_power(colapm_ctx* ctx, int nbins, double kmin, double kmax,
                  double* k_out, double* p_out, long long* nmodes_out);
 
+/* §7.1: cross-correlation coefficient r(k) = <Re delta_a delta_b^*> / sqrt(<|delta_a|^2> <|delta_b|^2>)
+ * of the density fields of the current particles of two contexts with the same np, nm and box (the
+ * printed formula lacks the square root, without which r is not dimensionless; it is read as
+ * intended). Both fields are the fixed-point CIC deposits of colapm_power on a's mesh; the sums run
+ * over the modes of each bin as in colapm_power (same bins, exclusions and full-grid mode counts),
+ * without the window (it is not part of the definition). Outputs (caller-owned, host or device,
+ * nbins each): mean |k|, r, mode count (NaN where a bin is empty). a may equal b (r = 1).
+ * COLAPM_E_ARG for mismatched sizes, COLAPM_E_STATE before initial conditions. Runs on a's stream
+ * after waiting for b's; synchronises. */
+int colapm_cross_correlation(colapm_ctx* a, colapm_ctx* b, int nbins, double kmin, double kmax,
+                             double* k_out, double* r_out, long long* nmodes_out);
+
 /* Positions (xyz, Mpc/h, in [0, L)) and momenta (xyz, Mpc/h) of all particles; either pointer
  * may be NULL. Host or device. Synchronises. */
 int colapm_get_particles(colapm_ctx* ctx, float* pos, float* mom);

@@ -56,6 +56,7 @@ def _load():
         "colapm_step": (I, [P, I]),
         "colapm_finalize": (I, [P]),
         "colapm_power": (I, [P, I, D, D, P, P, P]),
+        "colapm_cross_correlation": (I, [P, P, I, D, D, P, P, P]),
         "colapm_get_particles": (I, [P, P, P]),
         "colapm_get_particles_async": (I, [P, P, P]),
         "colapm_wait_particles": (I, [P]),
@@ -174,6 +175,15 @@ def colapm_power(ctx, nbins, kmin=0.0, kmax=0.0, k_out=None, p_out=None, n_out=N
     n_out = np.empty(nbins, dtype=np.int64) if n_out is None else n_out
     _check(LIB.colapm_power(ctx, nbins, kmin, kmax, _ptr(k_out), _ptr(p_out), _ptr(n_out)), "colapm_power")
     return k_out, p_out, n_out
+
+
+def colapm_cross_correlation(a, b, nbins, kmin=0.0, kmax=0.0, k_out=None, r_out=None, n_out=None):
+    k_out = np.empty(nbins) if k_out is None else k_out
+    r_out = np.empty(nbins) if r_out is None else r_out
+    n_out = np.empty(nbins, dtype=np.int64) if n_out is None else n_out
+    _check(LIB.colapm_cross_correlation(a, b, nbins, kmin, kmax, _ptr(k_out), _ptr(r_out), _ptr(n_out)),
+           "colapm_cross_correlation")
+    return k_out, r_out, n_out
 
 
 def colapm_get_particles(ctx, pos=None, mom=None):

@@ -34,7 +34,7 @@ struct colapm_ctx {
     bool xfer_pending = false;           // a copy out of xfer may still be running
     float2* tw_m = nullptr;              // exp(-2 pi i t / nm)
     float2* tw_p = nullptr;              // exp(-2 pi i t / np)
-    float* sinc2_m = nullptr;            // sinc^2(pi n / nm) per FFT bin
+    float* sinc2_m = nullptr;            // sinc^2(pi n / nm) per FFT bin, then nm ones (no window)
     float* amp_p = nullptr;              // Gaussian-field amplitude per integer |n|^2 of the IC grid
     int* err = nullptr;                  // device error bits: 1 overflow, 2 bad state import, 4 wait timeout
     // power-spectrum tables (grown on demand)
@@ -151,11 +151,15 @@ int copy_out(colapm_ctx* c, void* dst, const void* src, size_t bytes) {
     return COLAPM_OK;
 }
 
-int deposit(colapm_ctx* c) {
+// Fixed-point CIC deposit into c's mesh of the particles of `src` (default: c's own), and, when
+// `add` is given, of its particles as well (same mesh size; the masses add exactly).
+int deposit(colapm_ctx* c, const colapm_ctx* src = nullptr, const colapm_ctx* add = nullptr) {
     Phase ph(c, COLAPM_PHASE_DEPOSIT);
     if (!c->rho_clean) CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
     c->rho_clean = false;
-    CKL(launch_deposit(c->pos, c->np3, c->nm, c->rho, c->stream, c->block));
+    if (!src) src = c;
+    CKL(launch_deposit(src->pos, src->np3, c->nm, c->rho, c->stream, c->block));
+    if (add) CKL(launch_deposit(add->pos, add->np3, c->nm, c->rho, c->stream, c->block));
     return COLAPM_OK;
 }
 
@@ -326,7 +330,7 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
               dalloc(&c->pos, c->np3) == cudaSuccess && dalloc(&c->mom, 3 * c->np3) == cudaSuccess &&
               dalloc(&c->psi1, 3 * c->np3) == cudaSuccess && dalloc(&c->psi2, 3 * c->np3) == cudaSuccess &&
               dalloc(&c->scratch, 9 * c->np3) == cudaSuccess && dalloc(&c->tw_m, (size_t)c->nm) == cudaSuccess &&
-              dalloc(&c->tw_p, (size_t)c->np) == cudaSuccess && dalloc(&c->sinc2_m, (size_t)c->nm) == cudaSuccess &&
+              dalloc(&c->tw_p, (size_t)c->np) == cudaSuccess && dalloc(&c->sinc2_m, 2 * (size_t)c->nm) == cudaSuccess &&
               dalloc(&c->amp_p, (size_t)3 * (c->np / 2) * (c->np / 2) + 1) == cudaSuccess &&
               dalloc(&c->err, 4) == cudaSuccess && dalloc(&c->d_seed, 1) == cudaSuccess;
     if (ok && xy_supported(c->nm))
@@ -341,7 +345,7 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
         return COLAPM_E_NOMEM;
     }
     std::vector<float2> tm = twiddles(c->nm), tp = twiddles(c->np);
-    std::vector<float> s2(c->nm);
+    std::vector<float> s2(2 * c->nm, 1.0f);
     for (int i = 0; i < c->nm; ++i) {
         const int s = i < c->nm / 2 ? i : i - c->nm;
         const double x = M_PI * s / c->nm;
@@ -514,12 +518,15 @@ struct PhaseMute {   // time the nested deposit and forward passes under the enc
     ~PhaseMute() { --c->phase_mute; }
 };
 
-int power_enqueue(colapm_ctx* c, int nbins) {
+// The density deposited is that of `src`'s particles (default: c's own) plus those of `add`;
+// `window` = false bins |delta_k|^2 without dividing by the CIC window.
+int power_enqueue(colapm_ctx* c, int nbins, const colapm_ctx* src = nullptr, const colapm_ctx* add = nullptr,
+                  bool window = true) {
     const double box = c->prm.box;
     Phase ph(c, COLAPM_PHASE_POWER);   // all of P(k), its deposit and forward passes included
     PhaseMute mute(c);
     CK(cudaMemsetAsync(c->pw_acc, 0, (size_t)3 * nbins * sizeof(double), c->stream));
-    int r = deposit(c);
+    int r = deposit(c, src, add);
     if (r) return r;
     r = density_xy(c);
     if (r) return r;
@@ -532,7 +539,7 @@ int power_enqueue(colapm_ctx* c, int nbins) {
     pw.nbins = nbins;
     const double nm = c->nm;
     pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
-    CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m, 0, 1.0f, &pw,
+    CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m + (window ? 0 : c->nm), 0, 1.0f, &pw,
                   c->stream, c->two_stage, use_blocked(c)));
     return COLAPM_OK;
 }
@@ -571,6 +578,40 @@ int colapm_power(colapm_ctx* c, int nbins, double kmin, double kmax, double* k_o
     CK(cudaMemcpyAsync(p_out, po.data(), nbins * sizeof(double), cudaMemcpyDefault, c->stream));
     CK(cudaMemcpyAsync(nmodes_out, no.data(), nbins * sizeof(long long), cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return COLAPM_OK;
+}
+
+int colapm_cross_correlation(colapm_ctx* a, colapm_ctx* b, int nbins, double kmin, double kmax, double* k_out,
+                             double* r_out, long long* nmodes_out) {
+    if (!a || !b || !k_out || !r_out || !nmodes_out) return COLAPM_E_ARG;
+    if (!a->has_ics || !b->has_ics) return COLAPM_E_STATE;
+    if (a->np != b->np || a->nm != b->nm || a->prm.box != b->prm.box) return COLAPM_E_ARG;
+    CK(cudaStreamSynchronize(b->stream));   // b's particles are complete before a's stream reads them
+    int r = power_prepare(a, nbins, kmin, kmax);
+    if (r) return r;
+    // Bin sums of |delta_a|^2, |delta_b|^2 and |delta_a + delta_b|^2 (the masses of both deposited
+    // into one mesh; the transform is linear), without the window: Re(delta_a delta_b^*) is half of
+    // the third minus the first two, mode by mode, so also bin by bin.
+    std::vector<double> acc(9 * (size_t)nbins);
+    const colapm_ctx* src[3] = {a, b, a};
+    for (int pass = 0; pass < 3; ++pass) {
+        r = power_enqueue(a, nbins, src[pass], pass == 2 ? b : nullptr, false);
+        if (r) return r;
+        CK(cudaMemcpyAsync(acc.data() + (size_t)pass * 3 * nbins, a->pw_acc, 3 * (size_t)nbins * sizeof(double),
+                           cudaMemcpyDeviceToHost, a->stream));
+        r = pending_error(a);   // synchronises
+        if (r) return r;
+    }
+    std::vector<double> ko(nbins), ro(nbins), pa(nbins), pb(nbins), pab(nbins);
+    std::vector<long long> no(nbins);
+    power_finish(acc.data(), nbins, ko.data(), pa.data(), no.data());
+    power_finish(acc.data() + 3 * (size_t)nbins, nbins, ko.data(), pb.data(), no.data());
+    power_finish(acc.data() + 6 * (size_t)nbins, nbins, ko.data(), pab.data(), no.data());
+    for (int i = 0; i < nbins; ++i) ro[i] = no[i] ? 0.5 * (pab[i] - pa[i] - pb[i]) / std::sqrt(pa[i] * pb[i]) : NAN;
+    CK(cudaMemcpyAsync(k_out, ko.data(), nbins * sizeof(double), cudaMemcpyDefault, a->stream));
+    CK(cudaMemcpyAsync(r_out, ro.data(), nbins * sizeof(double), cudaMemcpyDefault, a->stream));
+    CK(cudaMemcpyAsync(nmodes_out, no.data(), nbins * sizeof(long long), cudaMemcpyDefault, a->stream));
+    CK(cudaStreamSynchronize(a->stream));
     return COLAPM_OK;
 }
 

@@ -34,6 +34,8 @@ class Pairs:
         n3 = self.np ** 3
         self.cc = C.colapm_create(coarse_params, stream)
         self.cf = C.colapm_create(fine_params, stream)
+        self.cx = C.colapm_create(coarse_params, stream)   # partner context of the cross-correlations
+        C.colapm_make_ics(self.cx)                          # (its particles are placed by displacement)
         self.coarse, self.target, self.pk_coarse, self.pk_fine = [], [], [], []
         self.nm = coarse_params.nm
         self.secs = {"coarse": 0.0, "fine": 0.0}
@@ -67,6 +69,7 @@ class Pairs:
     def close(self):
         C.colapm_destroy(self.cc)
         C.colapm_destroy(self.cf)
+        C.colapm_destroy(self.cx)
 
 
 def train(net, pairs, idx, steps, seed=0, log_every=0):
@@ -106,10 +109,11 @@ def evaluate(net, pairs, idx, cross_seeds=0):
         C.colapm_set_displacement(pairs.cc, out)
         _, p, _ = C.colapm_power(pairs.cc, pairs.nbins, 0.0, pairs.kmax)
         pk_net.append(p)
-        if j < cross_seeds:
-            fine = density_k(pairs, pairs.coarse[i] + pairs.target[i])
-            r_net.append(cross(density_k(pairs, out), fine, pairs))
-            r_plain.append(cross(density_k(pairs, pairs.coarse[i]), fine, pairs))
+        if j < cross_seeds:   # the coarse context holds the corrected particles here
+            C.colapm_set_displacement(pairs.cx, pairs.coarse[i] + pairs.target[i])
+            r_net.append(C.colapm_cross_correlation(pairs.cc, pairs.cx, pairs.nbins, 0.0, pairs.kmax)[1])
+            C.colapm_set_displacement(pairs.cc, pairs.coarse[i])
+            r_plain.append(C.colapm_cross_correlation(pairs.cc, pairs.cx, pairs.nbins, 0.0, pairs.kmax)[1])
     ok = pairs.nmodes > 0
     pf = np.mean([pairs.pk_fine[i] for i in idx], axis=0)[ok]
     pc = np.mean([pairs.pk_coarse[i] for i in idx], axis=0)[ok]
@@ -121,32 +125,3 @@ def evaluate(net, pairs, idx, cross_seeds=0):
         res["r_plain"] = np.mean(r_plain, axis=0).tolist()
         res["r_net"] = np.mean(r_net, axis=0).tolist()
     return res
-
-
-def density_k(pairs, psi):
-    """Fourier transform of the CIC density (mesh = particle grid) of the particles at q + psi."""
-    C.colapm_set_displacement(pairs.cc, psi)
-    n = pairs.nm
-    mesh = np.empty((n, n, n), np.int64)
-    C.colapm_get_density(pairs.cc, mesh)
-    rho = mesh.astype(np.float64)
-    return np.fft.rfftn(rho / rho.mean() - 1.0)
-
-
-def cross(da, db, pairs):
-    """r(k) = <da db*> / sqrt(<|da|^2> <|db|^2>) in the P(k) bins (log-spaced from 2 pi / L to kmax)."""
-    n = pairs.nm
-    kf = 2 * np.pi / pairs.box
-    kx = np.fft.fftfreq(n, 1.0 / n)
-    kz = np.fft.rfftfreq(n, 1.0 / n)
-    kk = kf * np.sqrt(kx[:, None, None] ** 2 + kx[None, :, None] ** 2 + kz[None, None, :] ** 2)
-    edges = kf * (pairs.kmax / kf) ** (np.arange(pairs.nbins + 1) / pairs.nbins)
-    b = np.digitize(kk, edges) - 1
-    sel = (b >= 0) & (b < pairs.nbins) & (kk > 0)
-    w = np.ones_like(kk)
-    w[..., 1:-1] = 2.0                                  # the half spectrum counts each mode twice
-    ab = np.bincount(b[sel], (w * (da * np.conj(db)).real)[sel], pairs.nbins)
-    aa = np.bincount(b[sel], (w * np.abs(da) ** 2)[sel], pairs.nbins)
-    bb = np.bincount(b[sel], (w * np.abs(db) ** 2)[sel], pairs.nbins)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        return ab / np.sqrt(aa * bb)

@@ -153,10 +153,10 @@ def test_force_mesh_matches_oracle(C, np_, nm, deconv):
 
 # --- one step from a shared state ----------------------------------------------------------
 
-@pytest.mark.parametrize("cola_on,stepping", [(1, 0), (0, 0), (1, 1)])
-def test_single_step_matches_oracle(C, cola_on, stepping):
+@pytest.mark.parametrize("cola_on,stepping,spacing", [(1, 0, 0), (0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)])
+def test_single_step_matches_oracle(C, cola_on, stepping, spacing):
     np_, nm = 32, 64
-    s = Sim(C, np=np_, nm=nm, box=256.0, cola=cola_on, stepping=stepping, seed=5)
+    s = Sim(C, np=np_, nm=nm, box=256.0, cola=cola_on, stepping=stepping, spacing=spacing, seed=5)
     try:
         C.colapm_make_ics(s.ctx)
         C.colapm_step(s.ctx, 3)                       # evolve a little, then compare one step
@@ -222,6 +222,47 @@ def test_power_on_shared_positions(C, nbins, kmin, kmax):
         assert np.max(np.abs(pk[ok] / pr[ok] - 1)) < 1e-4
     finally:
         s.close()
+
+
+def test_cross_correlation_matches_oracle(C):
+    # Two fields of the same seed, one COLA and one plain PM: correlated at low k, less so near the
+    # mesh scale. The library bins Re(delta_a delta_b^*) from |delta_a + delta_b|^2 - |delta_a|^2 -
+    # |delta_b|^2; the oracle bins the products directly (§7.1).
+    np_, nm, box = 32, 64, 256.0
+    a, b = Sim(C, np=np_, nm=nm, box=box, seed=8), Sim(C, np=np_, nm=nm, box=box, seed=8, cola=0, n_steps=4)
+    try:
+        for s in (a, b):
+            C.colapm_make_ics(s.ctx)
+            C.colapm_step(s.ctx, -1)
+        dks = []
+        for s in (a, b):
+            cell, off, _ = s.state()
+            rho = opm.cic_deposit(mesh_coords(cell, off), nm)
+            dks.append(np.fft.fftn(opm.density_contrast(rho, np_, nm)))
+        for nbins, kmin, kmax in ((40, 0.0, 0.0), (12, 0.05, 0.5)):
+            k, r, cnt = C.colapm_cross_correlation(a.ctx, b.ctx, nbins, kmin, kmax)
+            kf = 2 * math.pi / box
+            lo, hi = kmin or kf, kmax or math.pi * nm / box
+            rr = opower.cross_correlation(dks[0], dks[1], box, nbins, lo, hi)
+            _, _, nr = opower.binned_power(dks[0], box, nbins, lo, hi, window=False)
+            assert np.array_equal(cnt, nr)
+            ok = nr > 0
+            assert np.max(np.abs(r[ok] - rr[ok])) < 1e-5
+            assert np.isnan(r[~ok]).all()
+        assert np.nanmin(r) < 0.999 and np.nanmax(r) > 0.9     # a non-trivial test: r spans a range
+        _, r1, _ = C.colapm_cross_correlation(a.ctx, a.ctx, 12)
+        assert np.nanmax(np.abs(r1 - 1)) < 1e-6
+        with pytest.raises(C.ColapmError) as e:
+            other = Sim(C, np=np_, nm=2 * nm, box=box)
+            try:
+                C.colapm_make_ics(other.ctx)
+                C.colapm_cross_correlation(a.ctx, other.ctx, 12)
+            finally:
+                other.close()
+        assert e.value.code == -1
+    finally:
+        a.close()
+        b.close()
 
 
 def test_finalize_adds_lpt_momentum(C):
