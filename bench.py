@@ -41,6 +41,8 @@ ALG_PHASE = {
     "gather": ("particle", 80),  # read pos, mom, psi1, psi2, write pos, mom (+12 B/cell below)
 }
 EXTRA = {"deposit": ("particle", 16), "gather": ("cell", 12)}
+# The phases of a COLA step (the reordering of the particles by cell included when it runs).
+STEP_PHASES = ("sort", "deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather")
 # Single-kernel phases, and the DRAM bytes (read + write) ncu measured for each kernel at
 # 256^3 particles / 512^3 mesh (per launch, MB), scaled to other sizes with N_m = 2 N_p by the
 # cell count: force z pass 538.8 + 1017.2, inverse x 1610.7 + 1561.6, force y inverse
@@ -78,6 +80,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--sort", type=int, default=None,
+                    help="reorder the particles by cell every K steps (profiling aid; the default is the library's)")
     ap.add_argument("--engine", default="default", choices=["default", "fused", "two_stage", "stockham"],
                     help="FFT engine of the timed context (profiling aid; the default is the library's)")
     return ap.parse_args()
@@ -432,6 +436,8 @@ def main():
     if args.engine != "default":   # (fused x-y bits, two-stage) as colapm_set_engine takes them
         fused, two = {"fused": (3, 1), "two_stage": (0, 1), "stockham": (0, 0)}[args.engine]
         C.colapm_set_engine(ctx, fused, two, 256)
+    if args.sort is not None:
+        C.colapm_set_sort(ctx, args.sort)
     nbins = 100
     kd = torch.empty(nbins, dtype=torch.float64, device="cuda")
     pd = torch.empty(nbins, dtype=torch.float64, device="cuda")
@@ -513,8 +519,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": roof,
         # all step phases over the steps (P(k) times its deposit and forward passes as its own phase)
-        "cola_step_ms": sum(phase_ms[p] for p in ("deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", "gather"))
-                        / max(int(phase_n["gather"]), 1),
+        "cola_step_ms": sum(phase_ms[p] for p in STEP_PHASES) / max(int(phase_n["gather"]), 1),
         "cola_step_roofline_frac": None,
         "phase_ms_per_mock": {k: v / args.steps for k, v in phase_ms.items()},
         "clocks": clk.summary(),

@@ -211,6 +211,7 @@ enum {
     COLAPM_PHASE_POWER,         /* all of colapm_power: its deposit, forward passes,
                                    z transform and binning                          */
     COLAPM_PHASE_FFT_INV_X,     /* x inverse pass of the three forces (c2r)         */
+    COLAPM_PHASE_SORT,          /* reordering of the particle arrays by mesh cell   */
     COLAPM_PHASE_COUNT
 };
 int colapm_set_timing(colapm_ctx* ctx, int on);
@@ -234,6 +235,16 @@ int colapm_autotune(colapm_ctx* ctx, int* choice);
  * two-stage register FFT (else Stockham) and the particle-kernel block size (128, 256 or 512);
  * COLAPM_E_ARG otherwise. All engines compute the same transforms and agree to FP32 rounding. */
 int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
+
+/* Reorder the particle arrays by mesh cell before every `every`-th step (0: never, the default
+ * unless colapm_autotune chose otherwise). The analogue of the paper's particle migration (§4),
+ * which keeps each rank's particles with its slab of the mesh: here it keeps a warp's particles
+ * on neighbouring mesh cells, so that the deposit and the gather read and write runs of cells as
+ * structure grows. It is a counting sort of all particle arrays by bucket (z, y, x / 64) of the
+ * particle's cell; results do not depend on it (every step is per particle or an exact integer
+ * sum), and calls that take or return particle arrays still use particle-id order.
+ * COLAPM_E_ARG for every < 0. */
+int colapm_set_sort(colapm_ctx* ctx, int every);
 
 /* ---- batched mocks (many independent realisations of uneven sizes) ----------------------- */
 typedef struct colapm_batch colapm_batch;   /* opaque; owns its contexts and graph */

@@ -17,7 +17,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcolapm.so")
 
 SOURCES = ["colapm.cu", "fft_x.cu", "fft_y.cu", "fft_z.cu", "fft_xy.cu", "pm_kernels.cu", "ics_kernels.cu",
-           "cosmology.cpp", "noalloc.cu", "nn.cu"]
+           "sort_kernels.cu", "cosmology.cpp", "noalloc.cu", "nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 

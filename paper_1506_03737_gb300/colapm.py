@@ -12,7 +12,7 @@ import numpy as np
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libcolapm.so")
 
-PHASES = ["deposit", "fft_fwd", "poisson", "fft_inv", "gather", "ics", "power", "fft_inv_x"]
+PHASES = ["deposit", "fft_fwd", "poisson", "fft_inv", "gather", "ics", "power", "fft_inv_x", "sort"]
 
 
 class ColapmError(RuntimeError):
@@ -78,6 +78,7 @@ def _load():
         "colapm_power_noalloc": (I, [P, P, ctypes.c_longlong, I, D, I, D, D, P, P, P, P]),
         "colapm_autotune": (I, [P, P]),
         "colapm_set_engine": (I, [P, I, I, I]),
+        "colapm_set_sort": (I, [P, I]),
         "colapm_batch_create": (I, [I, P, I, P, ctypes.POINTER(P)]),
         "colapm_batch_run": (I, [P, P, I, D, D, P, P, P]),
         "colapm_batch_streams": (I, [P]),
@@ -301,6 +302,10 @@ def colapm_batch_streams(b):
 
 def colapm_batch_destroy(b):
     LIB.colapm_batch_destroy(b)
+
+
+def colapm_set_sort(ctx, every):
+    _check(LIB.colapm_set_sort(ctx, every), "colapm_set_sort")
 
 
 def colapm_set_timing(ctx, on=True):

@@ -28,6 +28,16 @@ struct colapm_ctx {
     float* psi1 = nullptr;               // 3 np^3, cells
     float* psi2 = nullptr;               // 3 np^3, cells
     float* scratch = nullptr;            // 9 np^3 (IC spectra and phi_ij; staging for state I/O)
+    int* id = nullptr;                   // np^3: particle id of each slot of pos, mom, psi1, psi2
+    float4* pos_alt = nullptr;           // second set of particle arrays: the target of a reordering
+    float* mom_alt = nullptr;
+    float* psi1_alt = nullptr;
+    float* psi2_alt = nullptr;
+    int* id_alt = nullptr;
+    unsigned* sort_cnt = nullptr;        // bucket counters / cursors of the cell sort
+    unsigned* sort_tile = nullptr;       // their tile sums
+    int sort_every = 0;                  // reorder by cell before every k-th step (0: never)
+    bool id_order = true;                // slots hold the particles in id order
     float* xfer = nullptr;               // 6 np^3: staging of the asynchronous catalogue copy (lazy)
     cudaStream_t xfer_stream = nullptr;  // its copy stream
     cudaEvent_t xfer_ready = nullptr, xfer_done = nullptr;
@@ -36,7 +46,8 @@ struct colapm_ctx {
     float2* tw_p = nullptr;              // exp(-2 pi i t / np)
     float* sinc2_m = nullptr;            // sinc^2(pi n / nm) per FFT bin, then nm ones (no window)
     float* amp_p = nullptr;              // Gaussian-field amplitude per integer |n|^2 of the IC grid
-    int* err = nullptr;                  // device error bits: 1 overflow, 2 bad state import, 4 wait timeout
+    int* err = nullptr;                  // device error bits: 1 overflow, 2 bad state import, 4 wait timeout,
+                                         // 8 internal (a sort slot out of range)
     // power-spectrum tables (grown on demand)
     int* pw_bin = nullptr;               // |n|^2 thresholds of the bins
     double* pw_acc = nullptr;            // ksum[nb], psum[nb], cnt[nb] (as u64)
@@ -112,7 +123,8 @@ bool is_device_ptr(const void* p) {
 void free_all(colapm_ctx* c) {
     if (c->xfer_stream) cudaStreamSynchronize(c->xfer_stream);
     void* ptrs[] = {c->rho, c->F, c->Freal, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
-                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed, c->xy_ring, c->xy_ctr, c->xfer};
+                    c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed, c->xy_ring, c->xy_ctr, c->xfer,
+                    c->id, c->pos_alt, c->mom_alt, c->psi1_alt, c->psi2_alt, c->id_alt, c->sort_cnt, c->sort_tile};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& v : c->ev)
@@ -142,6 +154,7 @@ int pending_error(colapm_ctx* c) {
     if (h & 1) return COLAPM_E_OVERFLOW;
     if (h & 2) return COLAPM_E_ARG;
     if (h & 4) return COLAPM_E_TIMEOUT;
+    if (h & 8) return COLAPM_E_CUDA;
     return COLAPM_OK;
 }
 
@@ -171,6 +184,37 @@ bool use_blocked(const colapm_ctx* c) { return c->two_stage && !(c->fused & 3) &
 
 // The three real force meshes of the last force computation.
 const float* force_mesh(const colapm_ctx* c) { return use_blocked(c) ? c->Freal : c->F; }
+
+SortBuffers sort_buffers(colapm_ctx* c) {
+    return SortBuffers{c->pos, c->mom, c->psi1, c->psi2, c->id, c->pos_alt, c->mom_alt, c->psi1_alt, c->psi2_alt,
+                       c->id_alt, c->sort_cnt, c->sort_tile, c->err};
+}
+
+void swap_particle_arrays(colapm_ctx* c) {
+    std::swap(c->pos, c->pos_alt);
+    std::swap(c->mom, c->mom_alt);
+    std::swap(c->psi1, c->psi1_alt);
+    std::swap(c->psi2, c->psi2_alt);
+    std::swap(c->id, c->id_alt);
+}
+
+// Reorder the particle arrays by mesh cell (counting sort into the second set, then swap).
+int sort_particles(colapm_ctx* c) {
+    Phase ph(c, COLAPM_PHASE_SORT);
+    CKL(launch_sort(sort_buffers(c), c->np3, c->nm, c->stream));
+    swap_particle_arrays(c);
+    c->id_order = false;
+    return COLAPM_OK;
+}
+
+// Put the particles back in id order (for the calls that exchange particle data in id order).
+int id_order(colapm_ctx* c) {
+    if (c->id_order) return COLAPM_OK;
+    CKL(launch_unsort(sort_buffers(c), c->np3, c->stream));
+    swap_particle_arrays(c);
+    c->id_order = true;
+    return COLAPM_OK;
+}
 
 float density_scale(const colapm_ctx* c) {
     const double m = (double)c->nm / c->np;
@@ -251,6 +295,8 @@ StepCoef coef_for(const colapm_ctx* c, int i) {
 // Particles from the LPT fields in psi1/psi2 (units: to_mesh converts them to mesh cells).
 int place_particles(colapm_ctx* c, float to_mesh) {
     const Growth& g = c->table.g[0];
+    CKL(launch_iota(c->id, c->np3, c->stream));
+    c->id_order = true;
     CKL(launch_init_particles(c->pos, c->mom, c->psi1, c->psi2, c->np, c->nm, to_mesh, (float)g.d1, (float)g.d2,
                              (float)g.p1, (float)g.p2, c->prm.cola, c->stream));
     c->step = 0;
@@ -332,7 +378,12 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
               dalloc(&c->scratch, 9 * c->np3) == cudaSuccess && dalloc(&c->tw_m, (size_t)c->nm) == cudaSuccess &&
               dalloc(&c->tw_p, (size_t)c->np) == cudaSuccess && dalloc(&c->sinc2_m, 2 * (size_t)c->nm) == cudaSuccess &&
               dalloc(&c->amp_p, (size_t)3 * (c->np / 2) * (c->np / 2) + 1) == cudaSuccess &&
-              dalloc(&c->err, 4) == cudaSuccess && dalloc(&c->d_seed, 1) == cudaSuccess;
+              dalloc(&c->err, 4) == cudaSuccess && dalloc(&c->d_seed, 1) == cudaSuccess &&
+              dalloc(&c->id, c->np3) == cudaSuccess && dalloc(&c->pos_alt, c->np3) == cudaSuccess &&
+              dalloc(&c->mom_alt, 3 * c->np3) == cudaSuccess && dalloc(&c->psi1_alt, 3 * c->np3) == cudaSuccess &&
+              dalloc(&c->psi2_alt, 3 * c->np3) == cudaSuccess && dalloc(&c->id_alt, c->np3) == cudaSuccess &&
+              dalloc(&c->sort_cnt, sort_buckets(c->nm)) == cudaSuccess &&
+              dalloc(&c->sort_tile, sort_tiles(c->nm)) == cudaSuccess;
     if (ok && xy_supported(c->nm))
         ok = dalloc(reinterpret_cast<char**>(&c->xy_ring), xy_ring_bytes(c->nm)) == cudaSuccess &&
              dalloc(&c->xy_ctr, xy_ctr_ints(c->nm, 3)) == cudaSuccess;
@@ -416,6 +467,7 @@ int colapm_make_ics(colapm_ctx* c) {
 
 int colapm_set_displacements(colapm_ctx* c, const float* psi1, const float* psi2) {
     if (!c || !psi1 || !psi2) return COLAPM_E_ARG;
+    c->id_order = true;   // the fields arrive in id order; place_particles resets the ids
     CK(cudaMemcpyAsync(c->psi1, psi1, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->stream));
     CK(cudaMemcpyAsync(c->psi2, psi2, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->stream));
     int r = place_particles(c, (float)(c->nm / c->prm.box));
@@ -431,6 +483,10 @@ int colapm_step(colapm_ctx* c, int k) {
     if (k < 0) k = left;
     if (k > left) return COLAPM_E_STATE;
     for (int s = 0; s < k; ++s) {
+        if (c->sort_every > 0 && c->step > 0 && c->step % c->sort_every == 0) {
+            int r = sort_particles(c);
+            if (r) return r;
+        }
         int r = compute_force(c);
         if (r) return r;
         Phase ph(c, COLAPM_PHASE_GATHER);
@@ -621,7 +677,7 @@ int colapm_get_particles(colapm_ctx* c, float* pos, float* mom) {
     const float cell = (float)(c->prm.box / c->nm);
     float* dp = pos && !is_device_ptr(pos) ? c->scratch : pos;
     float* dm = mom && !is_device_ptr(mom) ? c->scratch + 3 * c->np3 : mom;
-    CKL(launch_export_particles(c->pos, c->mom, c->np3, c->nm, cell, dp, dm, c->stream));
+    CKL(launch_export_particles(c->pos, c->mom, c->id_order ? nullptr : c->id, c->np3, c->nm, cell, dp, dm, c->stream));
     if (pos && dp != pos) copy_out(c, pos, dp, 3 * c->np3 * sizeof(float));
     if (mom && dm != mom) copy_out(c, mom, dm, 3 * c->np3 * sizeof(float));
     return pending_error(c);
@@ -644,7 +700,7 @@ int colapm_get_particles_async(colapm_ctx* c, float* pos, float* mom) {
     const float cell = (float)(c->prm.box / c->nm);
     float* dp = c->xfer;
     float* dm = c->xfer + 3 * c->np3;
-    CKL(launch_export_particles(c->pos, c->mom, c->np3, c->nm, cell, dp, dm, c->stream));
+    CKL(launch_export_particles(c->pos, c->mom, c->id_order ? nullptr : c->id, c->np3, c->nm, cell, dp, dm, c->stream));
     CK(cudaEventRecord(c->xfer_ready, c->stream));
     CK(cudaStreamWaitEvent(c->xfer_stream, c->xfer_ready, 0));
     if (pos) CK(cudaMemcpyAsync(pos, dp, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->xfer_stream));
@@ -666,6 +722,7 @@ int colapm_wait_particles(colapm_ctx* c) {
 int colapm_get_state(colapm_ctx* c, int* cell, float* off, float* mom) {
     if (!c) return COLAPM_E_ARG;
     if (!c->has_ics) return COLAPM_E_STATE;
+    if (int r = id_order(c)) return r;
     const size_t n = 3 * c->np3;
     int* dc = cell && !is_device_ptr(cell) ? reinterpret_cast<int*>(c->scratch) : cell;
     float* doff = off && !is_device_ptr(off) ? c->scratch + n : off;
@@ -680,6 +737,7 @@ int colapm_get_state(colapm_ctx* c, int* cell, float* off, float* mom) {
 int colapm_set_state(colapm_ctx* c, const int* cell, const float* off, const float* mom) {
     if (!c || (!cell != !off) || (!cell && !mom)) return COLAPM_E_ARG;
     if (!c->has_ics) return COLAPM_E_STATE;
+    if (int r = id_order(c)) return r;
     const size_t n = 3 * c->np3;
     const int* dc = cell;
     const float* doff = off;
@@ -703,6 +761,7 @@ int colapm_set_state(colapm_ctx* c, const int* cell, const float* off, const flo
 int colapm_get_displacement(colapm_ctx* c, float* psi) {
     if (!c || !psi) return COLAPM_E_ARG;
     if (!c->has_ics) return COLAPM_E_STATE;
+    if (int r = id_order(c)) return r;
     float* d = is_device_ptr(psi) ? psi : c->scratch;
     CKL(launch_export_displacement(c->pos, c->np, c->nm, (float)(c->prm.box / c->nm), d, c->stream));
     if (d != psi) copy_out(c, psi, d, 3 * c->np3 * sizeof(float));
@@ -712,6 +771,7 @@ int colapm_get_displacement(colapm_ctx* c, float* psi) {
 int colapm_set_displacement(colapm_ctx* c, const float* psi) {
     if (!c || !psi) return COLAPM_E_ARG;
     if (!c->has_ics) return COLAPM_E_STATE;
+    if (int r = id_order(c)) return r;
     const float* d = psi;
     if (!is_device_ptr(psi)) {
         CK(cudaMemcpyAsync(c->scratch, psi, 3 * c->np3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -742,6 +802,7 @@ int colapm_get_force(colapm_ctx* c, float* force) {
 int colapm_get_lpt(colapm_ctx* c, float* psi1, float* psi2) {
     if (!c) return COLAPM_E_ARG;
     if (!c->has_ics) return COLAPM_E_STATE;
+    if (int r = id_order(c)) return r;
     const float f = (float)(c->prm.box / c->nm);
     const size_t n = 3 * c->np3;
     if (psi1) {
@@ -784,6 +845,9 @@ static const unsigned long long kStateMagic = 0x434f4c41504d3031ull;   // "COLAP
 int colapm_save_state(colapm_ctx* c, void* buf, size_t* n) {
     if (!c || !n) return COLAPM_E_ARG;
     if (!c->has_ics) return COLAPM_E_STATE;
+    if (buf) {
+        if (int r = id_order(c)) return r;   // the state is saved in id order
+    }
     const size_t hdr = 8 * sizeof(long long);
     const size_t need = hdr + c->np3 * sizeof(float4) + 9 * c->np3 * sizeof(float);
     if (!buf) {
@@ -824,6 +888,8 @@ int colapm_load_state(colapm_ctx* c, const void* buf, size_t n) {
         CK(cudaMemcpyAsync(dst, b + o, 3 * c->np3 * sizeof(float), cudaMemcpyDefault, c->stream));
         o += 3 * c->np3 * sizeof(float);
     }
+    CKL(launch_iota(c->id, c->np3, c->stream));
+    c->id_order = true;
     CK(cudaStreamSynchronize(c->stream));
     c->step = (int)h[3];
     c->finalized = h[4] != 0;
@@ -871,6 +937,12 @@ int colapm_set_engine(colapm_ctx* c, int fused, int two_stage, int block) {
     c->fused = fused;
     c->two_stage = two_stage != 0;
     c->block = block;
+    return COLAPM_OK;
+}
+
+int colapm_set_sort(colapm_ctx* c, int every) {
+    if (!c || every < 0) return COLAPM_E_ARG;
+    c->sort_every = every;
     return COLAPM_OK;
 }
 

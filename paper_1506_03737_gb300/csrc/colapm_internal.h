@@ -106,7 +106,8 @@ cudaError_t launch_init_particles(float4* pos, float* mom, float* psi1, float* p
                                   cudaStream_t s);
 cudaError_t launch_add_lpt_momentum(float* mom, const float* psi1, const float* psi2, size_t np3, float p1,
                                     float p2, cudaStream_t s);
-cudaError_t launch_export_particles(const float4* pos, const float* mom, size_t np3, int nm, float cell,
+// Writes particle p's values at its id (id may be NULL: slot order is id order).
+cudaError_t launch_export_particles(const float4* pos, const float* mom, const int* id, size_t np3, int nm, float cell,
                                     float* pos_xyz, float* mom_xyz, cudaStream_t s);
 cudaError_t launch_export_state(const float4* pos, const float* mom, size_t np3, int nm, int* cell_xyz,
                                 float* off_xyz, float* mom_xyz, cudaStream_t s);
@@ -116,6 +117,32 @@ cudaError_t launch_export_displacement(const float4* pos, int np, int nm, float 
 cudaError_t launch_import_displacement(float4* pos, int np, int nm, float to_mesh, const float* psi, int* err,
                                        cudaStream_t s);
 cudaError_t launch_scale(float* dst, const float* src, size_t n, float f, cudaStream_t s);
+
+// --- launchers (sort_kernels.cu) ------------------------------------------------------------
+// Particle arrays in and out of a reordering, and the bucket counters of the sort.
+struct SortBuffers {
+    const float4* pos;
+    const float* mom;
+    const float* psi1;
+    const float* psi2;
+    const int* id;
+    float4* pos_o;
+    float* mom_o;
+    float* psi1_o;
+    float* psi2_o;
+    int* id_o;
+    unsigned* cnt;        // sort_buckets(nm): counts, then cursors
+    unsigned* tile_sum;   // sort_tiles(nm)
+    int* err;             // error bits; 8: a scatter slot out of range (an internal inconsistency)
+};
+int sort_xshift(int nm);
+size_t sort_buckets(int nm);
+size_t sort_tiles(int nm);
+// Counting sort of the particles by bucket (z, y, x >> sort_xshift) of their cell into the _o arrays.
+cudaError_t launch_sort(SortBuffers b, size_t np3, int nm, cudaStream_t s);
+// The _o arrays receive the particles in particle-id order (slot id[p] <- slot p), id_o the identity.
+cudaError_t launch_unsort(SortBuffers b, size_t np3, cudaStream_t s);
+cudaError_t launch_iota(int* id, size_t n, cudaStream_t s);
 
 // --- launchers (ics_kernels.cu) -----------------------------------------------------------
 // The seed is read from device memory, so a captured graph can be replayed with new seeds.

@@ -164,21 +164,23 @@ __global__ void k_add_lpt_momentum(float* __restrict__ mom, const float* __restr
     mom[i] = fmaf(p1, psi1[i], fmaf(p2, psi2[i], mom[i]));
 }
 
-__global__ void k_export_particles(const float4* __restrict__ pos, const float* __restrict__ mom, size_t np3, int nm,
-                                   float cell, float* __restrict__ pos_xyz, float* __restrict__ mom_xyz) {
+__global__ void k_export_particles(const float4* __restrict__ pos, const float* __restrict__ mom,
+                                   const int* __restrict__ id, size_t np3, int nm, float cell,
+                                   float* __restrict__ pos_xyz, float* __restrict__ mom_xyz) {
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
+    const size_t q = id ? (size_t)id[p] : p;   // the particle's id: its place in the output
     if (pos_xyz) {
         const float4 P = pos[p];
         const unsigned c = __float_as_uint(P.w), u = (unsigned)nm;
         const unsigned cx = c % u, cy = (c / u) % u, cz = c / (u * u);
-        pos_xyz[3 * p + 0] = ((float)cx + P.x) * cell;
-        pos_xyz[3 * p + 1] = ((float)cy + P.y) * cell;
-        pos_xyz[3 * p + 2] = ((float)cz + P.z) * cell;
+        pos_xyz[3 * q + 0] = ((float)cx + P.x) * cell;
+        pos_xyz[3 * q + 1] = ((float)cy + P.y) * cell;
+        pos_xyz[3 * q + 2] = ((float)cz + P.z) * cell;
     }
     if (mom_xyz) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) mom_xyz[3 * p + j] = mom[j * np3 + p] * cell;
+        for (int j = 0; j < 3; ++j) mom_xyz[3 * q + j] = mom[j * np3 + p] * cell;
     }
 }
 
@@ -317,9 +319,9 @@ cudaError_t launch_add_lpt_momentum(float* mom, const float* psi1, const float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_particles(const float4* pos, const float* mom, size_t np3, int nm, float cell,
+cudaError_t launch_export_particles(const float4* pos, const float* mom, const int* id, size_t np3, int nm, float cell,
                                     float* pos_xyz, float* mom_xyz, cudaStream_t s) {
-    k_export_particles<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, np3, nm, cell, pos_xyz, mom_xyz);
+    k_export_particles<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, id, np3, nm, cell, pos_xyz, mom_xyz);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,239 @@
+// Ordering of the particle arrays by mesh cell (the analogue, on one GPU, of the particle
+// migration of §4 that keeps each rank's particles with its slab of the mesh).
+//
+// The deposit and the gather read and write the eight CIC corners of every particle. In particle-id
+// (Lagrangian) order a warp's particles start out as mesh neighbours, but as structure grows they
+// spread over more and more cache lines; with the arrays ordered by cell, a warp's corners are runs
+// of one or two mesh rows again. The order is a counting sort of the particles by bucket =
+// (z, y, x / XB) of their cell -- XB = 64 cells, so a bucket holds a few particles and the order
+// inside a bucket (which the scatter leaves to its atomics) changes nothing a warp reads.
+//
+// Every step of the method is per particle or an order-independent integer sum (the fixed-point
+// deposit), so the physics does not depend on the order; `id` keeps each slot's particle id for
+// the calls that exchange particle data in id order.
+#include "colapm_internal.h"
+
+namespace colapm {
+
+namespace {
+
+constexpr int SCAN_T = 1024;           // threads of the scan kernels
+constexpr int SCAN_PER = 4;            // elements per thread in the block scan
+constexpr int SCAN_TILE = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ unsigned bucket_of(float w, int nm, int xshift) {
+    const unsigned c = __float_as_uint(w), u = (unsigned)nm;   // linear cell x + nm (y + nm z)
+    const unsigned x = c % u, yz = c / u;
+    return yz * (u >> xshift) + (x >> xshift);
+}
+
+// Warp-aggregated increment: the lanes of a warp with the same bucket (in particle order a warp's
+// particles fill one or two buckets) make one atomic; each lane gets the old value plus its rank
+// among them. Lanes that have returned are not in the active mask.
+__device__ __forceinline__ unsigned warp_bucket_add(unsigned* ctr, unsigned b) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned peers = __match_any_sync(__activemask(), b);
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(ctr + b, (unsigned)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + (unsigned)__popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void k_sort_count(const float4* __restrict__ pos, size_t np3, int nm, int xshift, unsigned* __restrict__ cnt) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    warp_bucket_add(cnt, bucket_of(__ldg(&pos[p].w), nm, xshift));
+}
+
+// Exclusive scan of cnt[0..n) in tiles of SCAN_TILE: tile sums first, then the scan within tiles
+// offset by the scanned tile sums (written to both start and cursor).
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const unsigned* __restrict__ cnt, size_t n,
+                                                       unsigned* __restrict__ tile_sum) {
+    __shared__ unsigned part[SCAN_T / 32];
+    const size_t base = (size_t)blockIdx.x * SCAN_TILE;
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        const size_t i = base + (size_t)k * SCAN_T + threadIdx.x;
+        if (i < n) s += cnt[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned v = part[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) tile_sum[blockIdx.x] = v;
+    }
+}
+
+// One block scans the tile sums in place (exclusive), SCAN_T at a time with a running carry.
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(unsigned* __restrict__ tile_sum, int ntiles) {
+    __shared__ unsigned warp_tot[SCAN_T / 32];
+    __shared__ unsigned carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b = 0; b < ntiles; b += SCAN_T) {
+        const int i = b + threadIdx.x;
+        const unsigned v = i < ntiles ? tile_sum[i] : 0u;
+        unsigned x = v;   // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned t = warp_tot[lane];
+            unsigned ti = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+                if (lane >= o) ti += y;
+            }
+            warp_tot[lane] = ti - t;   // exclusive prefix of the warp totals
+        }
+        __syncthreads();
+        const unsigned c0 = carry;
+        if (i < ntiles) tile_sum[i] = c0 + warp_tot[wid] + x - v;
+        __syncthreads();
+        if (threadIdx.x == SCAN_T - 1) carry = c0 + warp_tot[wid] + x;
+        __syncthreads();
+    }
+}
+
+// (cnt and cursor may be the same array: each thread reads its elements before it writes them.)
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const unsigned* cnt, size_t n,
+                                                       const unsigned* __restrict__ tile_off, unsigned* cursor) {
+    __shared__ unsigned warp_tot[SCAN_T / 32];
+    const size_t base = (size_t)blockIdx.x * SCAN_TILE;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // thread t scans elements base + t * SCAN_PER .. + SCAN_PER - 1 (contiguous per thread)
+    unsigned v[SCAN_PER], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        const size_t i = base + (size_t)threadIdx.x * SCAN_PER + k;
+        v[k] = i < n ? cnt[i] : 0u;
+        s += v[k];
+    }
+    unsigned x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const unsigned t = warp_tot[lane];
+        unsigned ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        warp_tot[lane] = ti - t;
+    }
+    __syncthreads();
+    unsigned run = tile_off[blockIdx.x] + warp_tot[wid] + x - s;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER; ++k) {
+        const size_t i = base + (size_t)threadIdx.x * SCAN_PER + k;
+        if (i < n) cursor[i] = run;
+        run += v[k];
+    }
+}
+
+// Move every particle to the next free slot of its bucket (cursor[] starts at the bucket offsets).
+__global__ void k_sort_scatter(const float4* __restrict__ pos, const float* __restrict__ mom,
+                               const float* __restrict__ psi1, const float* __restrict__ psi2,
+                               const int* __restrict__ id, size_t np3, int nm, int xshift,
+                               unsigned* __restrict__ cursor, float4* __restrict__ pos_o, float* __restrict__ mom_o,
+                               float* __restrict__ psi1_o, float* __restrict__ psi2_o, int* __restrict__ id_o,
+                               int* err) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const float4 P = __ldcs(pos + p);
+    const size_t d = warp_bucket_add(cursor, bucket_of(P.w, nm, xshift));
+    if (d >= np3) {   // cannot happen with consistent counts; guards the writes below
+        atomicOr(err, 8);
+        return;
+    }
+    __stcs(pos_o + d, P);
+    id_o[d] = __ldcs(id + p);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        mom_o[j * np3 + d] = __ldcs(mom + j * np3 + p);
+        psi1_o[j * np3 + d] = __ldcs(psi1 + j * np3 + p);
+        psi2_o[j * np3 + d] = __ldcs(psi2 + j * np3 + p);
+    }
+}
+
+// Back to particle-id order: slot id[p] receives particle p's data.
+__global__ void k_unsort(const float4* __restrict__ pos, const float* __restrict__ mom, const float* __restrict__ psi1,
+                         const float* __restrict__ psi2, const int* __restrict__ id, size_t np3,
+                         float4* __restrict__ pos_o, float* __restrict__ mom_o, float* __restrict__ psi1_o,
+                         float* __restrict__ psi2_o, int* __restrict__ id_o) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const int i = id[p];
+    pos_o[i] = pos[p];
+    id_o[i] = i;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        mom_o[j * np3 + i] = mom[j * np3 + p];
+        psi1_o[j * np3 + i] = psi1[j * np3 + p];
+        psi2_o[j * np3 + i] = psi2[j * np3 + p];
+    }
+}
+
+__global__ void k_iota(int* __restrict__ id, size_t n) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) id[p] = (int)p;
+}
+
+inline unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int sort_xshift(int nm) {
+    int s = 0;
+    while ((nm >> s) > 1 && (1 << s) < 64 && ((nm >> (s + 1)) << (s + 1)) == nm) ++s;
+    return s;   // x-block of 2^s cells: 64 where nm allows, else the largest power of two dividing nm
+}
+
+size_t sort_buckets(int nm) { return (size_t)nm * nm * (size_t)(nm >> sort_xshift(nm)); }
+
+size_t sort_tiles(int nm) { return (sort_buckets(nm) + SCAN_TILE - 1) / SCAN_TILE; }
+
+cudaError_t launch_sort(SortBuffers b, size_t np3, int nm, cudaStream_t s) {
+    const int xs = sort_xshift(nm);
+    const size_t nb = sort_buckets(nm), nt = sort_tiles(nm);
+    cudaError_t e = cudaMemsetAsync(b.cnt, 0, nb * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_sort_count<<<blocks(np3, 256), 256, 0, s>>>(b.pos, np3, nm, xs, b.cnt);
+    k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, s>>>(b.cnt, nb, b.tile_sum);
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(b.tile_sum, (int)nt);
+    k_scan_apply<<<(unsigned)nt, SCAN_T, 0, s>>>(b.cnt, nb, b.tile_sum, b.cnt);   // counts -> cursors in place
+    k_sort_scatter<<<blocks(np3, 256), 256, 0, s>>>(b.pos, b.mom, b.psi1, b.psi2, b.id, np3, nm, xs, b.cnt, b.pos_o,
+                                                     b.mom_o, b.psi1_o, b.psi2_o, b.id_o, b.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsort(SortBuffers b, size_t np3, cudaStream_t s) {
+    k_unsort<<<blocks(np3, 256), 256, 0, s>>>(b.pos, b.mom, b.psi1, b.psi2, b.id, np3, b.pos_o, b.mom_o, b.psi1_o,
+                                              b.psi2_o, b.id_o);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int* id, size_t n, cudaStream_t s) {
+    k_iota<<<blocks(n, 256), 256, 0, s>>>(id, n);
+    return cudaGetLastError();
+}
+
+}  // namespace colapm

@@ -286,6 +286,81 @@ def test_finalize_adds_lpt_momentum(C):
         s.close()
 
 
+# --- particle order ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("np_,nm,every", [(32, 64, 1), (64, 128, 3), (32, 96, 2)])
+def test_cell_order_changes_no_result(C, np_, nm, every):
+    """Reordering the particle arrays by cell is invisible: every step is per particle or an exact
+    integer sum, so runs with and without it give bit-identical catalogues, states, LPT fields,
+    densities, spectra and finalized momenta, in particle-id order."""
+    kw = dict(np=np_, nm=nm, box=200.0, seed=13, n_steps=6)
+    a, b = Sim(C, **kw), Sim(C, **kw)
+    try:
+        C.colapm_set_sort(b.ctx, every)
+        for s in (a, b):
+            C.colapm_make_ics(s.ctx)
+            C.colapm_step(s.ctx, 4)
+        for x, y in zip(a.state(), b.state()):
+            assert np.array_equal(x, y)
+        for x, y in zip(a.lpt(), b.lpt()):
+            assert np.array_equal(x, y)
+        for s in (a, b):
+            C.colapm_step(s.ctx, -1)
+        n = np_ ** 3
+        pa, ma = np.empty((n, 3), np.float32), np.empty((n, 3), np.float32)
+        pb, mb = np.empty((n, 3), np.float32), np.empty((n, 3), np.float32)
+        C.colapm_get_particles(a.ctx, pa, ma)
+        C.colapm_get_particles(b.ctx, pb, mb)
+        assert np.array_equal(pa, pb) and np.array_equal(ma, mb)
+        assert np.array_equal(a.density(), b.density())
+        ka, pka, na = C.colapm_power(a.ctx, 30)
+        kb, pkb, nb = C.colapm_power(b.ctx, 30)
+        assert np.array_equal(na, nb) and np.array_equal(pka, pkb, equal_nan=True)
+        psi_a, psi_b = np.empty((n, 3), np.float32), np.empty((n, 3), np.float32)
+        C.colapm_get_displacement(a.ctx, psi_a)
+        C.colapm_get_displacement(b.ctx, psi_b)
+        assert np.array_equal(psi_a, psi_b)
+        for s in (a, b):
+            C.colapm_finalize(s.ctx)
+        C.colapm_get_particles(a.ctx, None, ma)
+        C.colapm_get_particles(b.ctx, None, mb)
+        assert np.array_equal(ma, mb)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_cell_order_checkpoint_and_async_export(C):
+    kw = dict(np=32, nm=64, box=256.0, seed=14, n_steps=8)
+    a, b = Sim(C, **kw), Sim(C, **kw)
+    try:
+        C.colapm_set_sort(a.ctx, 1)
+        C.colapm_make_ics(a.ctx)
+        C.colapm_step(a.ctx, 5)                       # arrays in cell order here
+        buf = C.colapm_save_state(a.ctx)              # saved in id order
+        C.colapm_step(a.ctx, 1)                       # sorts again
+        C.colapm_load_state(b.ctx, buf)
+        C.colapm_step(b.ctx, 1)
+        for x, y in zip(a.state(), b.state()):
+            assert np.array_equal(x, y)
+        import torch
+        n = 32 ** 3
+        C.colapm_step(a.ctx, 1)
+        ref = np.empty((n, 3), np.float32)
+        C.colapm_get_particles(a.ctx, ref, None)
+        pos = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+        C.colapm_step(b.ctx, 1)
+        C.colapm_get_particles_async(a.ctx, pos, None)
+        C.colapm_wait_particles(a.ctx)
+        assert np.array_equal(pos.numpy(), ref)
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_set_sort(a.ctx, -1)
+        assert e.value.code == -1
+    finally:
+        a.close()
+        b.close()
+
+
 # --- error paths and state I/O ----------------------------------------------------------------
 
 def test_error_codes(C):
