@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-study", action="store_true")
     ap.add_argument("--sort", type=int, default=None,
                     help="reorder the particles by cell every K steps (profiling aid; the default is the library's)")
     ap.add_argument("--engine", default="default", choices=["default", "fused", "two_stage", "stockham"],
@@ -541,6 +542,16 @@ def main():
                     "(transforms), and with torch's elementwise operator multiplies (stage)"}
     if not args.no_batch:
         line["batch"] = run_batch(C, stream, rank, args, world, dist)
+    if not args.no_study and rank == 0:
+        from paper_1506_03737_gb300 import studies
+        t0 = time.perf_counter()
+        res = studies.run(256, 512.0, seeds=(1, 2), stream=stream.cuda_stream,
+                          cosmo={x: workloads.COSMO[x] for x in ("omega_m", "h", "n_s", "sigma8")})
+        line["accuracy_study"] = {
+            "workload": "256^3 particles, L = 512 Mpc/h, z 9 -> 0, 10 steps per variant, seeds 1 and 2; reference: "
+                        "COLA modified lin-a 50 steps on N_m = 512; all spectra on the 512^3 mesh, 24 log bins to "
+                        "the particle Nyquist frequency",
+            "seconds": time.perf_counter() - t0, "variants": studies.summary(res)}
     if not args.no_learned and rank == 0:   # one training run; the other ranks have nothing to add
         line["learned"] = run_learned(C, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -55,7 +55,8 @@ typedef struct {
     colapm_cosmo cosmo;
     double box;                 /* box side L, Mpc/h                                            */
     int np;                     /* particles per side N_p (even, 8..1024)                       */
-    int nm;                     /* PM mesh cells per side N_m (even, 8..1024, a multiple of N_p)*/
+    int nm;                     /* PM mesh cells per side N_m (even, 16..1024): a multiple of   */
+                                /* N_p, or N_p / 2 or N_p / 4 (coarser force mesh, §7.3)         */
     double z_init, z_final;     /* redshift of the 2LPT initial conditions and of the last step */
     int n_steps;                /* number of Kick-Drift steps (§2.3)                             */
     int spacing;                /* 0: steps linear in a (default), 1: logarithmic in a (§7.3)   */
@@ -95,6 +96,16 @@ int colapm_make_ics(colapm_ctx* ctx);
  * without reallocating). */
 int colapm_reseed(colapm_ctx* ctx, unsigned long long seed);
 
+/* §5: local primordial non-Gaussianity of the initial conditions made by the next colapm_make_ics
+ * (and returned by colapm_get_gaussian_field); 0 (the default) gives the Gaussian field. The Gaussian
+ * field delta_k = M(k) phi_k defines the primordial potential phi; in real space
+ * Phi = phi + f_NL (phi^2 - <phi^2>) (<> the box average), and the initial density is M(k) Phi_k, with
+ * M(k) = (2/3) (k c / H0)^2 T(k) D_md / Om (the Poisson equation in matter domination with the BBKS
+ * transfer function and D_md the z = 0 growth normalised to a in the matter era; Phi has the sign of
+ * the density, so f_NL > 0 skews it positively). The first non-zero call allocates two small tables
+ * (COLAPM_E_NOMEM on failure) and synchronises; COLAPM_E_ARG for a non-finite value. */
+int colapm_set_fnl(colapm_ctx* ctx, double fnl);
+
 /* Replace the LPT displacements with caller-supplied fields on the N_p^3 Lagrangian lattice
  * (c-major, 3 * Np^3 floats each, Mpc/h, host or device) and place the particles as
  * colapm_make_ics does. Used to start from a known field (parity tests, planted modes). */
@@ -118,6 +129,15 @@ int colapm_finalize(colapm_ctx* ctx);
  * kmin <= 0 selects 2 pi / L, kmax <= 0 selects pi N_m / L. Synchronises. */
 int colapm_power(colapm_ctx* ctx, int nbins, double kmin, double kmax,
                  double* k_out, double* p_out, long long* nmodes_out);
+
+/* §7.1: power spectrum in redshift space. Every particle is moved along the line of sight by
+ * s_los = v_los / (H(a) a), v the total peculiar velocity at a_N (the run must be finalized:
+ * COLAPM_E_STATE otherwise), the line of sight radial from an observer at the centre of the box
+ * (los = -1, the paper's choice) or along axis los = 0, 1, 2 (plane-parallel); redshift-space
+ * positions wrap periodically. Then as colapm_power (same bins, outputs and conventions); the
+ * particles themselves are not moved. Synchronises. */
+int colapm_power_rsd(colapm_ctx* ctx, int los, int nbins, double kmin, double kmax,
+                     double* k_out, double* p_out, long long* nmodes_out);
 
 /* §7.1: cross-correlation coefficient r(k) = <Re delta_a delta_b^*> / sqrt(<|delta_a|^2> <|delta_b|^2>)
  * of the density fields of the current particles of two contexts with the same np, nm and box (the

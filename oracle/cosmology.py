@@ -88,6 +88,12 @@ def growth(a, om):
     return y[0] / norm, y[2] / norm ** 2, y[1] / norm, y[3] / norm ** 2
 
 
+def growth_matter_era(om):
+    """D1(a = 1) normalised to D1 = a deep in matter domination (the growth of a density mode since the
+    matter era: the factor by which Lambda suppresses it, g(Om) in the literature)."""
+    return float(_growth_raw(np.array([1.0]), om)[0, 0])
+
+
 def _quad(f, lo, hi):
     if hi == lo:
         return 0.0

@@ -92,6 +92,44 @@ def gaussian_field(n, box, seed, pk):
     return full
 
 
+# Hubble distance c / H0 in Mpc/h (H0 = 100 h km/s/Mpc, c = 299792.458 km/s).
+HUBBLE_DISTANCE = 2997.92458
+
+
+def potential_to_density(n, box, om, h, d_md):
+    """M(k) on the full [z][y][x] grid: delta_k(z = 0) = M(k) Phi_k for the primordial potential Phi
+    in matter domination (the Poisson equation with the transfer function and the growth from the
+    matter era to z = 0): M = (2/3) (k c / H0)^2 T_BBKS(k) d_md / Om, with d_md the z = 0 growth
+    factor normalised to a in matter domination. Zero at k = 0. Sign: Phi and delta have the same
+    sign (Phi is minus the Newtonian potential, the convention in which f_NL > 0 skews the density
+    positively)."""
+    from .cosmology import t_bbks
+    kx, ky, kz, _ = wavevectors(n, box)
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    m = np.zeros_like(k)
+    ok = k > 0
+    m[ok] = 2.0 / 3.0 * (k[ok] * HUBBLE_DISTANCE) ** 2 * t_bbks(k[ok], om, h) * d_md / om
+    return m
+
+
+def local_fnl_field(delta_k, box, fnl, om, h, d_md, fft=None):
+    """Local primordial non-Gaussianity (§5): the Gaussian field delta_k = M phi_k defines the Gaussian
+    potential phi; in real space Phi = phi + f_NL (phi^2 - <phi^2>) (<> the box average), and the
+    initial density is M Phi_k, zero at k = 0 and on the Nyquist planes. f_NL = 0 returns delta_k."""
+    fftn_, ifftn_ = (np.fft.fftn, np.fft.ifftn) if fft == "numpy" else (fftn, ifftn)
+    n = delta_k.shape[0]
+    m = potential_to_density(n, box, om, h, d_md)
+    phi_k = np.zeros_like(delta_k)
+    ok = m > 0
+    phi_k[ok] = delta_k[ok] / m[ok]
+    phi = ifftn_(phi_k).real
+    big_phi = phi + fnl * (phi * phi - np.mean(phi * phi))
+    out = m * fftn_(big_phi)
+    _, _, _, nyq = wavevectors(n, box)
+    out[nyq] = 0.0
+    return out
+
+
 def lpt_displacements(delta_k, box, fft=None):
     """Return (Psi1, Psi2), each (3, N, N, N) real [component x,y,z][iz][iy][ix], in Mpc/h.
 

@@ -14,6 +14,12 @@ mean |k|, the mean P and the mode count. Shot noise is not subtracted (§7.1).
 Cross-correlation (§7.1): r(k) = <Re delta_a delta_b^*> / sqrt(<|delta_a|^2> <|delta_b|^2>)
 per bin. The printed formula lacks the square root; without it r is not
 dimensionless, so the square root is read as intended.
+
+Redshift space (§7.1): each particle is moved along the line of sight by
+s_los = v_los / (H(a) a). With the momentum p = a^3 E dx/da of the method (H0 = 1, lengths
+in Mpc/h) the peculiar velocity is v = a dx/dt = p / a and H = E(a). The line of sight is
+radial from an observer at the centre of the box (the paper's choice) or, as an option, one
+of the axes (plane-parallel). Redshift-space positions wrap periodically.
 """
 import math
 
@@ -21,7 +27,7 @@ import numpy as np
 
 from .fft import fftn
 from .ics import wavevectors
-from . import pm
+from . import cosmology, pm
 
 
 def bin_edges(nbins, kmin, kmax):
@@ -74,3 +80,22 @@ def cross_correlation(dka, dkb, box, nbins, kmin, kmax):
     cbb = np.bincount(b[sel], weights=(np.abs(dkb) ** 2)[sel], minlength=nbins)
     with np.errstate(invalid="ignore", divide="ignore"):
         return cab / np.sqrt(caa * cbb)
+
+
+def redshift_space(x, p, a, om, box, los=-1):
+    """Redshift-space positions (P,3) of particles at x (Mpc/h) with momenta p (Mpc/h) at scale
+    factor a (§7.1): los = -1 radial from the box centre, 0/1/2 along that axis."""
+    x = np.asarray(x, dtype=np.float64)
+    v = np.asarray(p, dtype=np.float64) / a
+    scale = 1.0 / (cosmology.hubble_e(a, om) * a)
+    if los < 0:
+        r = x - 0.5 * box
+        d = np.sqrt(np.sum(r * r, axis=1))
+        rhat = np.zeros_like(r)
+        ok = d > 0
+        rhat[ok] = r[ok] / d[ok, None]
+        s = x + (np.sum(v * rhat, axis=1) * scale)[:, None] * rhat
+    else:
+        s = x.copy()
+        s[:, los] += v[:, los] * scale
+    return np.mod(s, box)

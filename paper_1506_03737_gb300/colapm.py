@@ -57,6 +57,8 @@ def _load():
         "colapm_finalize": (I, [P]),
         "colapm_power": (I, [P, I, D, D, P, P, P]),
         "colapm_cross_correlation": (I, [P, P, I, D, D, P, P, P]),
+        "colapm_power_rsd": (I, [P, I, I, D, D, P, P, P]),
+        "colapm_set_fnl": (I, [P, D]),
         "colapm_get_particles": (I, [P, P, P]),
         "colapm_get_particles_async": (I, [P, P, P]),
         "colapm_wait_particles": (I, [P]),
@@ -175,6 +177,18 @@ def colapm_power(ctx, nbins, kmin=0.0, kmax=0.0, k_out=None, p_out=None, n_out=N
     p_out = np.empty(nbins) if p_out is None else p_out
     n_out = np.empty(nbins, dtype=np.int64) if n_out is None else n_out
     _check(LIB.colapm_power(ctx, nbins, kmin, kmax, _ptr(k_out), _ptr(p_out), _ptr(n_out)), "colapm_power")
+    return k_out, p_out, n_out
+
+
+def colapm_set_fnl(ctx, fnl):
+    _check(LIB.colapm_set_fnl(ctx, float(fnl)), "colapm_set_fnl")
+
+
+def colapm_power_rsd(ctx, los, nbins, kmin=0.0, kmax=0.0, k_out=None, p_out=None, n_out=None):
+    k_out = np.empty(nbins) if k_out is None else k_out
+    p_out = np.empty(nbins) if p_out is None else p_out
+    n_out = np.empty(nbins, dtype=np.int64) if n_out is None else n_out
+    _check(LIB.colapm_power_rsd(ctx, los, nbins, kmin, kmax, _ptr(k_out), _ptr(p_out), _ptr(n_out)), "colapm_power_rsd")
     return k_out, p_out, n_out
 
 

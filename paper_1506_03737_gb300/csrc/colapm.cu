@@ -37,6 +37,9 @@ struct colapm_ctx {
     unsigned* sort_cnt = nullptr;        // bucket counters / cursors of the cell sort
     unsigned* sort_tile = nullptr;       // their tile sums
     int sort_every = 0;                  // reorder by cell before every k-th step (0: never)
+    double fnl = 0.0;                    // local primordial non-Gaussianity of the next ICs
+    float* fnl_tab = nullptr;            // per |n|^2 of the IC grid: 1 / (M N^3), then M (colapm_set_fnl)
+    double* fnl_sum = nullptr;           // FP64 sum of phi^2
     bool id_order = true;                // slots hold the particles in id order
     float* xfer = nullptr;               // 6 np^3: staging of the asynchronous catalogue copy (lazy)
     cudaStream_t xfer_stream = nullptr;  // its copy stream
@@ -124,7 +127,8 @@ void free_all(colapm_ctx* c) {
     if (c->xfer_stream) cudaStreamSynchronize(c->xfer_stream);
     void* ptrs[] = {c->rho, c->F, c->Freal, c->pos, c->mom, c->psi1, c->psi2, c->scratch, c->tw_m, c->tw_p,
                     c->sinc2_m, c->amp_p, c->err, c->pw_bin, c->pw_acc, c->d_seed, c->xy_ring, c->xy_ctr, c->xfer,
-                    c->id, c->pos_alt, c->mom_alt, c->psi1_alt, c->psi2_alt, c->id_alt, c->sort_cnt, c->sort_tile};
+                    c->id, c->pos_alt, c->mom_alt, c->psi1_alt, c->psi2_alt, c->id_alt, c->sort_cnt, c->sort_tile,
+                    c->fnl_tab, c->fnl_sum};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& v : c->ev)
@@ -164,15 +168,27 @@ int copy_out(colapm_ctx* c, void* dst, const void* src, size_t bytes) {
     return COLAPM_OK;
 }
 
-// Fixed-point CIC deposit into c's mesh of the particles of `src` (default: c's own), and, when
-// `add` is given, of its particles as well (same mesh size; the masses add exactly).
-int deposit(colapm_ctx* c, const colapm_ctx* src = nullptr, const colapm_ctx* add = nullptr) {
+// Particle positions to deposit: up to two arrays (cell bits + offsets on c's mesh) whose masses add.
+struct DepositSrc {
+    const float4* pos[2] = {nullptr, nullptr};
+    size_t n[2] = {0, 0};
+};
+
+DepositSrc own_particles(const colapm_ctx* c) {
+    DepositSrc d;
+    d.pos[0] = c->pos;
+    d.n[0] = c->np3;
+    return d;
+}
+
+// Fixed-point CIC deposit into c's mesh of the given particles (default: c's own).
+int deposit(colapm_ctx* c, const DepositSrc* src = nullptr) {
     Phase ph(c, COLAPM_PHASE_DEPOSIT);
     if (!c->rho_clean) CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
     c->rho_clean = false;
-    if (!src) src = c;
-    CKL(launch_deposit(src->pos, src->np3, c->nm, c->rho, c->stream, c->block));
-    if (add) CKL(launch_deposit(add->pos, add->np3, c->nm, c->rho, c->stream, c->block));
+    const DepositSrc d = src ? *src : own_particles(c);
+    for (int i = 0; i < 2; ++i)
+        if (d.pos[i]) CKL(launch_deposit(d.pos[i], d.n[i], c->nm, c->rho, c->stream, c->block));
     return COLAPM_OK;
 }
 
@@ -305,9 +321,31 @@ int place_particles(colapm_ctx* c, float to_mesh) {
     return COLAPM_OK;
 }
 
+// The initial density field delta_k at z = 0 on the IC grid's half spectrum (§5): the Gaussian field,
+// and, with f_NL != 0, the local transform of its primordial potential (transforms on the
+// Stockham engine; `work` holds N_p^3 floats of scratch).
+int initial_field(colapm_ctx* c, float2* dk, float2* work) {
+    const int np = c->np;
+    CKL(launch_gaussian_field(np, c->seed_src, c->amp_p, dk, c->stream));
+    if (c->fnl == 0.0) return COLAPM_OK;
+    const size_t ntab = (size_t)3 * (np / 2) * (np / 2) + 1;
+    ZOut o{};
+    o.p[0] = dk;
+    CKL(launch_fz(np, Z_SCALE_INV, dk, o, c->tw_p, c->fnl_tab, 0, 1.0f, nullptr, c->stream, false));   // phi_k, z inverse
+    CKL(launch_fy(np, +1, dk, 0, 1, c->tw_p, c->stream, false));
+    CKL(launch_fx_inv(np, dk, 0, 1, c->tw_p, c->stream, false));                                       // phi(x)
+    CKL(launch_local_fnl(reinterpret_cast<float*>(dk), c->np3, c->fnl, c->fnl_sum, c->stream));       // Phi(x)
+    CKL(launch_fx_fwd_f32(np, reinterpret_cast<float*>(dk), work, c->tw_p, c->stream, false));
+    CKL(launch_fy(np, -1, work, 0, 1, c->tw_p, c->stream, false));
+    CKL(launch_fz(np, Z_SCALE_FWD, work, o, c->tw_p, c->fnl_tab + ntab, 0, 1.0f, nullptr, c->stream, false));   // M Phi_k
+    return COLAPM_OK;
+}
+
 int validate(const colapm_params* p) {
     if (!p) return COLAPM_E_ARG;
-    if (!supported_size(p->np) || !supported_size(p->nm) || p->nm % p->np != 0) return COLAPM_E_ARG;
+    // N_m a multiple of N_p, or a coarser mesh with N_p = 2 N_m or 4 N_m (§7.3's mesh study)
+    if (!supported_size(p->np) || !supported_size(p->nm)) return COLAPM_E_ARG;
+    if (p->nm % p->np != 0 && p->np != 2 * p->nm && p->np != 4 * p->nm) return COLAPM_E_ARG;
     if (!(p->box > 0) || !(p->cosmo.omega_m > 0 && p->cosmo.omega_m <= 1) || !(p->cosmo.h > 0) ||
         !(p->cosmo.sigma8 > 0))
         return COLAPM_E_ARG;
@@ -444,7 +482,7 @@ int colapm_make_ics(colapm_ctx* c) {
     float2* p2 = reinterpret_cast<float2*>(c->psi2);
     const float gnorm = (float)(1.0 / ((double)np * np * np));
     if (c->seed_src == c->d_seed) CKL(launch_set_u64(c->d_seed, c->prm.seed, c->stream));
-    CKL(launch_gaussian_field(np, c->seed_src, c->amp_p, dk, c->stream));
+    if (int r = initial_field(c, dk, phi)) return r;
     ZOut o1{};
     for (int j = 0; j < 3; ++j) o1.p[j] = p1 + j * hs;
     for (int j = 0; j < 6; ++j) o1.p[3 + j] = phi + j * hs;
@@ -574,15 +612,14 @@ struct PhaseMute {   // time the nested deposit and forward passes under the enc
     ~PhaseMute() { --c->phase_mute; }
 };
 
-// The density deposited is that of `src`'s particles (default: c's own) plus those of `add`;
-// `window` = false bins |delta_k|^2 without dividing by the CIC window.
-int power_enqueue(colapm_ctx* c, int nbins, const colapm_ctx* src = nullptr, const colapm_ctx* add = nullptr,
-                  bool window = true) {
+// The density deposited is that of `src` (default: c's own particles); `window` = false bins
+// |delta_k|^2 without dividing by the CIC window.
+int power_enqueue(colapm_ctx* c, int nbins, const DepositSrc* src = nullptr, bool window = true) {
     const double box = c->prm.box;
     Phase ph(c, COLAPM_PHASE_POWER);   // all of P(k), its deposit and forward passes included
     PhaseMute mute(c);
     CK(cudaMemsetAsync(c->pw_acc, 0, (size_t)3 * nbins * sizeof(double), c->stream));
-    int r = deposit(c, src, add);
+    int r = deposit(c, src);
     if (r) return r;
     r = density_xy(c);
     if (r) return r;
@@ -649,9 +686,14 @@ int colapm_cross_correlation(colapm_ctx* a, colapm_ctx* b, int nbins, double kmi
     // into one mesh; the transform is linear), without the window: Re(delta_a delta_b^*) is half of
     // the third minus the first two, mode by mode, so also bin by bin.
     std::vector<double> acc(9 * (size_t)nbins);
-    const colapm_ctx* src[3] = {a, b, a};
+    DepositSrc src[3];
+    src[0] = own_particles(a);
+    src[1] = own_particles(b);
+    src[2] = own_particles(a);
+    src[2].pos[1] = b->pos;
+    src[2].n[1] = b->np3;
     for (int pass = 0; pass < 3; ++pass) {
-        r = power_enqueue(a, nbins, src[pass], pass == 2 ? b : nullptr, false);
+        r = power_enqueue(a, nbins, &src[pass], false);
         if (r) return r;
         CK(cudaMemcpyAsync(acc.data() + (size_t)pass * 3 * nbins, a->pw_acc, 3 * (size_t)nbins * sizeof(double),
                            cudaMemcpyDeviceToHost, a->stream));
@@ -668,6 +710,35 @@ int colapm_cross_correlation(colapm_ctx* a, colapm_ctx* b, int nbins, double kmi
     CK(cudaMemcpyAsync(r_out, ro.data(), nbins * sizeof(double), cudaMemcpyDefault, a->stream));
     CK(cudaMemcpyAsync(nmodes_out, no.data(), nbins * sizeof(long long), cudaMemcpyDefault, a->stream));
     CK(cudaStreamSynchronize(a->stream));
+    return COLAPM_OK;
+}
+
+int colapm_power_rsd(colapm_ctx* c, int los, int nbins, double kmin, double kmax, double* k_out, double* p_out,
+                     long long* nmodes_out) {
+    if (!c || !k_out || !p_out || !nmodes_out || los < -1 || los > 2) return COLAPM_E_ARG;
+    if (!c->has_ics || !c->finalized) return COLAPM_E_STATE;   // total momenta at a_N
+    int r = power_prepare(c, nbins, kmin, kmax);
+    if (r) return r;
+    const double a = c->table.a[c->prm.n_steps], om = c->prm.cosmo.omega_m;
+    const double e = std::sqrt(om / (a * a * a) + 1.0 - om);
+    // the redshift-space positions go to the second particle array (free between calls)
+    CKL(launch_rsd_positions(c->pos, c->mom, c->np3, c->nm, (float)(1.0 / (a * a * e)), los, c->pos_alt, c->stream));
+    DepositSrc src;
+    src.pos[0] = c->pos_alt;
+    src.n[0] = c->np3;
+    r = power_enqueue(c, nbins, &src);
+    if (r) return r;
+    std::vector<double> acc(3 * nbins);
+    CK(cudaMemcpyAsync(acc.data(), c->pw_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    r = pending_error(c);
+    if (r) return r;
+    std::vector<double> ko(nbins), po(nbins);
+    std::vector<long long> no(nbins);
+    power_finish(acc.data(), nbins, ko.data(), po.data(), no.data());
+    CK(cudaMemcpyAsync(k_out, ko.data(), nbins * sizeof(double), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(p_out, po.data(), nbins * sizeof(double), cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(nmodes_out, no.data(), nbins * sizeof(long long), cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return COLAPM_OK;
 }
 
@@ -820,9 +891,39 @@ int colapm_get_lpt(colapm_ctx* c, float* psi1, float* psi2) {
 int colapm_get_gaussian_field(colapm_ctx* c, float* dk) {
     if (!c || !dk) return COLAPM_E_ARG;
     CKL(launch_set_u64(c->d_seed, c->prm.seed, c->stream));
-    CKL(launch_gaussian_field(c->np, c->d_seed, c->amp_p, reinterpret_cast<float2*>(c->scratch), c->stream));
+    const unsigned long long* src = c->seed_src;
+    c->seed_src = c->d_seed;
+    int r = initial_field(c, reinterpret_cast<float2*>(c->scratch), reinterpret_cast<float2*>(c->scratch + c->np3));
+    c->seed_src = src;
+    if (r) return r;
     copy_out(c, dk, c->scratch, c->np3 * sizeof(float));
     return pending_error(c);
+}
+
+int colapm_set_fnl(colapm_ctx* c, double fnl) {
+    if (!c || !std::isfinite(fnl)) return COLAPM_E_ARG;
+    if (fnl != 0.0 && !c->fnl_tab) {
+        const int h = c->np / 2;
+        const size_t ntab = (size_t)3 * h * h + 1;
+        if (dalloc(&c->fnl_tab, 2 * ntab) != cudaSuccess || dalloc(&c->fnl_sum, 1) != cudaSuccess) {
+            cudaGetLastError();
+            return COLAPM_E_NOMEM;
+        }
+        // M(k) = (2/3) (k c / H0)^2 T(k) D_md / Om per integer |n|^2 (k = 2 pi |n| / L), FP64 then FP32
+        const double om = c->prm.cosmo.omega_m, hh = c->prm.cosmo.h, dmd = growth_matter_era(om);
+        const double n3 = (double)c->np * c->np * c->np, chub = 2997.92458;
+        std::vector<float> tab(2 * ntab, 0.0f);
+        for (size_t n2 = 1; n2 < ntab; ++n2) {
+            const double k = 2.0 * M_PI * std::sqrt((double)n2) / c->prm.box;
+            const double m = 2.0 / 3.0 * (k * chub) * (k * chub) * bbks(k, om, hh) * dmd / om;
+            tab[n2] = (float)(1.0 / (m * n3));
+            tab[ntab + n2] = (float)m;
+        }
+        CK(cudaMemcpyAsync(c->fnl_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    c->fnl = fnl;
+    return COLAPM_OK;
 }
 
 int colapm_reseed(colapm_ctx* c, unsigned long long seed) {

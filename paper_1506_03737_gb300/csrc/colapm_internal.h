@@ -29,7 +29,10 @@ enum ZMode {
     Z_FORCE = 0,   // forward z, F_j = i k_j delta / (k^2 W^d) / N^3, inverse z, 3 outputs
     Z_LPT1 = 1,    // (input already transformed) Psi1_j = i k_j d/k^2, phi_ab = k_a k_b d/k^2, 9 outputs
     Z_LPT2 = 2,    // forward z, Psi2_j = -i k_j S/k^2, 3 outputs
-    Z_POWER = 3    // forward z, bin |delta|^2 / W^2
+    Z_POWER = 3,   // forward z, bin |delta|^2 / W^2
+    // (Stockham engine only) per-mode scaling by a table indexed by |n|^2, passed in place of sinc2:
+    Z_SCALE_FWD = 4,   // forward z, then multiply: 1 output in k-space
+    Z_SCALE_INV = 5    // (input already transformed) multiply, then inverse z: 1 output
 };
 
 // Power-spectrum binning. Bin membership is decided in FP64 on the host (or once per call on
@@ -117,6 +120,9 @@ cudaError_t launch_export_displacement(const float4* pos, int np, int nm, float 
 cudaError_t launch_import_displacement(float4* pos, int np, int nm, float to_mesh, const float* psi, int* err,
                                        cudaStream_t s);
 cudaError_t launch_scale(float* dst, const float* src, size_t n, float f, cudaStream_t s);
+// Redshift-space positions (cell bits + offsets) of the particles; scale = 1 / (a^2 E(a)).
+cudaError_t launch_rsd_positions(const float4* pos, const float* mom, size_t np3, int nm, float scale, int los,
+                                 float4* out, cudaStream_t s);
 
 // --- launchers (sort_kernels.cu) ------------------------------------------------------------
 // Particle arrays in and out of a reordering, and the bucket counters of the sort.
@@ -150,5 +156,8 @@ cudaError_t launch_gaussian_field(int np, const unsigned long long* seed, const 
                                   cudaStream_t s);
 cudaError_t launch_lpt2_source(const float* phi, size_t np3, float* src, cudaStream_t s);
 cudaError_t launch_set_u64(unsigned long long* dst, unsigned long long value, cudaStream_t s);
+// Local primordial non-Gaussianity on a real field of n values in place: Phi = phi + fnl (phi^2 - <phi^2>),
+// <> the mean over the field (FP64 sum into `sum2`, one double of scratch).
+cudaError_t launch_local_fnl(float* phi, size_t n, double fnl, double* sum2, cudaStream_t s);
 
 }  // namespace colapm

@@ -115,7 +115,13 @@ StepTable make_step_table(double om, double z_init, double z_final, int n_steps,
 }
 
 // BBKS transfer function, q = k / (Om h).
-static double bbks(double k, double om, double h) {
+double growth_matter_era(double om) {
+    double y[4];
+    growth_raw(1.0, om, y);
+    return y[0];   // D1(1) with D1 = a deep in matter domination
+}
+
+double bbks(double k, double om, double h) {
     const double q = k / (om * h);
     if (q < 1e-12) return 1.0;
     const double x = 2.34 * q;

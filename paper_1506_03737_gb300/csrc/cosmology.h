@@ -11,6 +11,13 @@ struct Growth {
 
 Growth growth_at(double a, double om);
 
+// D1(a = 1) normalised to D1 = a in matter domination (the growth of the primordial potential's
+// density from the matter era to z = 0).
+double growth_matter_era(double om);
+
+// BBKS (1986) transfer function, Gamma = om h, k in h/Mpc.
+double bbks(double k, double om, double h);
+
 struct StepTable {
     std::vector<double> a;       // a_0 .. a_N
     std::vector<Growth> g;       // growth at a_i

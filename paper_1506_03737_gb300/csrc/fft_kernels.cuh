@@ -306,9 +306,10 @@ __device__ __forceinline__ int signed_bin(int i, int L) { return i < L / 2 ? i :
 
 template <int MODE>
 struct ZCfg {
-    static constexpr bool FWD = MODE != Z_LPT1;                      // forward z transform first
-    static constexpr bool PREFETCH = MODE != Z_LPT1;                 // double-buffered input
-    static constexpr int NBASE = MODE == Z_LPT1 ? 3 : (MODE == Z_POWER ? 0 : 2);
+    static constexpr bool SCALE = MODE == Z_SCALE_FWD || MODE == Z_SCALE_INV;
+    static constexpr bool FWD = MODE != Z_LPT1 && MODE != Z_SCALE_INV;   // forward z transform first
+    static constexpr bool PREFETCH = FWD;                                // double-buffered input
+    static constexpr int NBASE = MODE == Z_LPT1 ? 3 : (MODE == Z_POWER || SCALE ? 0 : 2);
     static constexpr int NBUF = (PREFETCH ? 2 : 1) + (NBASE > 1 ? NBASE - 1 : 0);
 };
 
@@ -427,6 +428,20 @@ __global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
             }
             __syncthreads();
             continue;
+        } else if constexpr (Z::SCALE) {
+            // multiply every mode by the table value of its |n|^2 (sinc2 holds the table), zero on the
+            // Nyquist planes; then the inverse z transform (Z_SCALE_INV) or nothing (Z_SCALE_FWD)
+            for (int e = threadIdx.x; e < L * 8; e += T) {
+                const int z = e >> 3, c = e & 7;
+                const int nx = kx0 + c, nz = signed_bin(z, L);
+                const float m = nyq_y || z == L / 2 ? 0.0f : sinc2[nx * nx + ny * ny + nz * nz];
+                const int i2 = CT<L>::a2(z, c);
+                cur[i2] = cscale(cur[i2], m);
+            }
+            __syncthreads();
+            if constexpr (MODE == Z_SCALE_INV) tile_fft<L, T, +1, L>(cur, stw);
+            st_cols<L, T>(cur, out.p[0] + base, stride);
+            __syncthreads();
         } else {
             // bases: A = g v, B = k_z A (, C = k_z^2 A), g = gnorm / (k^2 [W^d]), 0 on excluded modes
             float4* c4 = reinterpret_cast<float4*>(cur);

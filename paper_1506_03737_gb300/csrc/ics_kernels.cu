@@ -80,7 +80,37 @@ __global__ void k_lpt2_source(const float* __restrict__ phi, size_t n3, float* _
 
 __global__ void k_set_u64(unsigned long long* dst, unsigned long long value) { *dst = value; }
 
+// Sum of phi^2 over the field: FP32 per thread over a grid-stride run, a warp sum, then one FP64
+// atomic per warp.
+__global__ void k_sum_sq(const float* __restrict__ phi, size_t n, double* __restrict__ sum2) {
+    double acc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = phi[i];
+        acc += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sum2, acc);
+}
+
+// Local non-Gaussianity (§5): Phi = phi + f_NL (phi^2 - <phi^2>).
+__global__ void k_local_fnl(float* __restrict__ phi, size_t n, float fnl, const double* __restrict__ sum2) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mean = (float)(*sum2 / (double)n);
+    const float v = phi[i];
+    phi[i] = fmaf(fnl, fmaf(v, v, -mean), v);
+}
+
 }  // namespace
+
+cudaError_t launch_local_fnl(float* phi, size_t n, double fnl, double* sum2, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(sum2, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    k_sum_sq<<<1024, 256, 0, s>>>(phi, n, sum2);
+    k_local_fnl<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(phi, n, (float)fnl, sum2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_u64(unsigned long long* dst, unsigned long long value, cudaStream_t s) {
     k_set_u64<<<1, 1, 0, s>>>(dst, value);

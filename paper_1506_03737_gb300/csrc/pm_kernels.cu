@@ -126,6 +126,15 @@ __global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict_
     __stcs(pos + p, make_float4(o[0], o[1], o[2], __uint_as_float(lin)));
 }
 
+// Site i of the Lagrangian lattice sits at mesh coordinate i nm / np + 1/2 (spacing L / np, offset by
+// half a PM cell). Integer part of i nm / np and its exact fractional remainder (0 when np divides nm;
+// a multiple of nm / np otherwise, i.e. of 1/2 or 1/4 for the coarse meshes).
+__device__ __forceinline__ void lattice_site(int i, int np, int nm, int& base, float& frac) {
+    const long long t = (long long)i * nm;
+    base = (int)(t / np);
+    frac = (float)(t % np) / (float)np;
+}
+
 // Particles on the Lagrangian lattice (offset by half a PM cell), displaced by D1 Psi1 + D2 Psi2.
 // psi1 / psi2 arrive in IC-grid cells and leave in PM-mesh cells (factor to_mesh = Nm / Np).
 __global__ void k_init_particles(float4* __restrict__ pos, float* __restrict__ mom, float* __restrict__ psi1,
@@ -134,7 +143,6 @@ __global__ void k_init_particles(float4* __restrict__ pos, float* __restrict__ m
     const size_t np3 = (size_t)np * np * np;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
-    const int ratio = nm / np;
     const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
     int cell[3];
     float o[3];
@@ -143,11 +151,14 @@ __global__ void k_init_particles(float4* __restrict__ pos, float* __restrict__ m
         const float s1 = psi1[j * np3 + p] * to_mesh, s2 = psi2[j * np3 + p] * to_mesh;
         psi1[j * np3 + p] = s1;
         psi2[j * np3 + p] = s2;
-        const float u = 0.5f + fmaf(d1, s1, d2 * s2);
+        int base;
+        float frac;
+        lattice_site(site[j], np, nm, base, frac);
+        const float u = (0.5f + frac) + fmaf(d1, s1, d2 * s2);
         float fl = floorf(u);
         float r = u - fl;
         if (r >= 1.0f) { r = 0.0f; fl += 1.0f; }
-        int cc = (site[j] * ratio + (int)fl) % nm;
+        int cc = (base + (int)fl) % nm;
         if (cc < 0) cc += nm;
         cell[j] = cc;
         o[j] = r;
@@ -245,12 +256,15 @@ __global__ void k_export_displacement(const float4* __restrict__ pos, int np, in
     const int cc[3] = {(int)(c % u), (int)((c / u) % u), (int)(c / (u * u))};
     const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
     const float off[3] = {P.x, P.y, P.z};
-    const int ratio = nm / np, h = nm / 2;
+    const int h = nm / 2;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        int di = cc[j] - site[j] * ratio;
+        int base;
+        float frac;
+        lattice_site(site[j], np, nm, base, frac);
+        int di = cc[j] - base;
         di += di < -h ? nm : (di >= h ? -nm : 0);
-        float d = (float)di + (off[j] - 0.5f);
+        float d = (float)di + (off[j] - (0.5f + frac));
         d += d < -(float)h ? (float)nm : (d >= (float)h ? -(float)nm : 0.0f);
         psi[3 * p + j] = d * cell;
     }
@@ -263,7 +277,6 @@ __global__ void k_import_displacement(float4* __restrict__ pos, int np, int nm, 
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
     const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
-    const int ratio = nm / np;
     int cell[3];
     float o[3];
 #pragma unroll
@@ -273,17 +286,65 @@ __global__ void k_import_displacement(float4* __restrict__ pos, int np, int nm, 
             atomicOr(err, 2);
             return;
         }
-        const float u = 0.5f + s;
+        int base;
+        float frac;
+        lattice_site(site[j], np, nm, base, frac);
+        const float u = (0.5f + frac) + s;
         float fl = floorf(u);
         float r = u - fl;
         if (r >= 1.0f) { r = 0.0f; fl += 1.0f; }
-        int cc = (site[j] * ratio + (int)fl) % nm;
+        int cc = (base + (int)fl) % nm;
         if (cc < 0) cc += nm;
         cell[j] = cc;
         o[j] = r;
     }
     const unsigned lin = (unsigned)cell[0] + (unsigned)nm * ((unsigned)cell[1] + (unsigned)nm * (unsigned)cell[2]);
     pos[p] = make_float4(o[0], o[1], o[2], __uint_as_float(lin));
+}
+
+// Redshift-space positions (§7.1): each particle moves by s_los = v_los / (a H) along the line of
+// sight. With momenta p in mesh units (the total momentum after finalisation) and H0 = 1, v = p / a and
+// H = E(a), so the shift in cells is p_los / (a^2 E) = p_los * scale. los < 0: radial from the box
+// centre (mesh coordinate nm/2 on every axis); los = 0, 1, 2: along that axis. The shift is added to
+// the offset and the cell renormalised with the periodic wrap, as in the drift.
+__global__ void k_rsd_positions(const float4* __restrict__ pos, const float* __restrict__ mom, size_t np3, int nm,
+                                float scale, int los, float4* __restrict__ out) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    const float4 P = pos[p];
+    const unsigned c = __float_as_uint(P.w), u = (unsigned)nm;
+    int cell[3] = {(int)(c % u), (int)((c / u) % u), (int)(c / (u * u))};
+    const float off[3] = {P.x, P.y, P.z};
+    const float v[3] = {mom[p], mom[np3 + p], mom[2 * np3 + p]};
+    float d[3] = {0.0f, 0.0f, 0.0f};
+    if (los < 0) {
+        float r[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) r[j] = (float)(cell[j] - nm / 2) + off[j];   // exact integer part
+        const float rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        if (rr > 0.0f) {
+            const float inv = rsqrtf(rr);
+            const float vl = (v[0] * r[0] + v[1] * r[1] + v[2] * r[2]) * inv * scale;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) d[j] = vl * r[j] * inv;
+        }
+    } else {
+        d[los] = v[los] * scale;
+    }
+    float o[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float w = off[j] + d[j];
+        float fl = floorf(w);
+        float rem = w - fl;
+        if (rem >= 1.0f) { rem = 0.0f; fl += 1.0f; }
+        int cc = (cell[j] + (int)fl) % nm;
+        if (cc < 0) cc += nm;
+        cell[j] = cc;
+        o[j] = rem;
+    }
+    const unsigned lin = (unsigned)cell[0] + u * ((unsigned)cell[1] + u * (unsigned)cell[2]);
+    out[p] = make_float4(o[0], o[1], o[2], __uint_as_float(lin));
 }
 
 __global__ void k_scale(float* __restrict__ dst, const float* __restrict__ src, size_t n, float f) {
@@ -347,6 +408,12 @@ cudaError_t launch_import_displacement(float4* pos, int np, int nm, float to_mes
                                        cudaStream_t s) {
     const size_t np3 = (size_t)np * np * np;
     k_import_displacement<<<blocks(np3, 256), 256, 0, s>>>(pos, np, nm, to_mesh, psi, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rsd_positions(const float4* pos, const float* mom, size_t np3, int nm, float scale, int los,
+                                 float4* out, cudaStream_t s) {
+    k_rsd_positions<<<blocks(np3, 256), 256, 0, s>>>(pos, mom, np3, nm, scale, los, out);
     return cudaGetLastError();
 }
 

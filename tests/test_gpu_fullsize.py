@@ -126,6 +126,32 @@ def test_power_at_full_size_on_shared_positions(C, name, host_gb):
     assert np.max(np.abs(k[ok] / kr[ok] - 1)) < 1e-6
 
 
+@pytest.mark.parametrize("name,host_gb", [("cola_256p_512m_512mpc", 24), ("cola_512p_1024m_1024mpc", 190)])
+def test_redshift_space_power_at_full_size(C, name, host_gb):
+    need_host_gb(host_gb)
+    kw = workloads.run_params(name)
+    np_, nm, box = kw["np"], kw["nm"], kw["box"]
+    n = np_ ** 3
+    ctx = C.colapm_create(C.default_params(**kw))
+    try:
+        C.colapm_make_ics(ctx)
+        C.colapm_step(ctx, -1)
+        C.colapm_finalize(ctx)
+        k, pk, cnt = C.colapm_power_rsd(ctx, -1, 100)
+        cell, off, mom = np.empty((n, 3), np.int32), np.empty((n, 3), np.float32), np.empty((n, 3), np.float32)
+        C.colapm_get_state(ctx, cell, off, mom)
+    finally:
+        C.colapm_destroy(ctx)
+    x = (cell + off.astype(np.float64)) * (box / nm)
+    del cell, off
+    xs = opower.redshift_space(x, mom.astype(np.float64) * (box / nm), 1.0, kw["omega_m"], box, -1)
+    del x, mom
+    kr, pr, nr = opower.power_from_positions(xs, box, np_, nm, 100, fft="numpy")
+    assert np.array_equal(cnt, nr)
+    ok = nr > 0
+    assert np.max(np.abs(pk[ok] / pr[ok] - 1)) < 1e-4
+
+
 # --- force on a clustered 3-D state --------------------------------------------------------------
 
 @pytest.mark.parametrize("np_,nm,box", [(256, 512, 512.0), (160, 320, 300.0), (192, 384, 400.0)])

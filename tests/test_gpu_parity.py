@@ -90,6 +90,44 @@ def test_gaussian_field_matches_oracle(C, np_, seed):
         s.close()
 
 
+@pytest.mark.parametrize("np_", [32, 64])
+def test_local_fnl_initial_field_matches_oracle(C, np_):
+    # §5: local f_NL on the primordial potential; the GPU runs its transforms on the Stockham engine.
+    box, seed = 256.0, 9
+    s = Sim(C, np=np_, nm=np_, box=box, seed=seed)
+    try:
+        half = lambda: np.empty(np_ ** 3, np.float32)                    # noqa: E731
+        g0 = half()
+        C.colapm_get_gaussian_field(s.ctx, g0)
+        C.colapm_set_fnl(s.ctx, 0.0)
+        g00 = half()
+        C.colapm_get_gaussian_field(s.ctx, g00)
+        assert np.array_equal(g0, g00)
+        pk = ocosmo.linear_pk(0.3, 0.7, 0.96, 0.8)
+        dk = oics.gaussian_field(np_, box, seed, pk)
+        dmd = ocosmo.growth_matter_era(0.3)
+        gau = g0.view(np.complex64).reshape(np_, np_, np_ // 2).astype(np.complex128)
+        for fnl in (300.0, -3000.0):
+            C.colapm_set_fnl(s.ctx, fnl)
+            g = half()
+            C.colapm_get_gaussian_field(s.ctx, g)
+            gpu = g.view(np.complex64).reshape(np_, np_, np_ // 2).astype(np.complex128)
+            ref = oics.local_fnl_field(dk, box, fnl, 0.3, 0.7, dmd)
+            assert np.abs(gpu - ref[:, :, : np_ // 2]).max() < 1e-5 * np.abs(ref).max()
+            ng_gpu, ng_ref = gpu - gau, (ref - dk)[:, :, : np_ // 2]
+            assert np.abs(ng_gpu - ng_ref).max() < 2e-3 * np.abs(ng_ref).max(), fnl
+        # the ICs of the last f_NL: LPT displacements from the oracle's non-Gaussian field
+        C.colapm_make_ics(s.ctx)
+        g1, g2 = s.lpt()
+        p1, p2 = oics.lpt_displacements(ref, box)
+        assert rel_rms(g1, p1) < 1e-5 and rel_rms(g2, p2) < 1e-4
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_set_fnl(s.ctx, float("nan"))
+        assert e.value.code == -1
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("np_,nm", [(32, 64), (64, 64)])
 def test_lpt_displacements_and_initial_positions(C, np_, nm):
     s = Sim(C, np=np_, nm=nm, box=256.0, seed=4)
@@ -116,7 +154,7 @@ def test_lpt_displacements_and_initial_positions(C, np_, nm):
 # --- deposit -------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("np_,nm,kind", [(32, 64, "random"), (32, 96, "random"), (64, 64, "clustered"),
-                                         (32, 160, "random")])
+                                         (32, 160, "random"), (64, 32, "random"), (64, 16, "clustered")])
 def test_density_bit_exact(C, np_, nm, kind):
     s = Sim(C, np=np_, nm=nm, box=200.0)
     try:
@@ -135,7 +173,8 @@ def test_density_bit_exact(C, np_, nm, kind):
 
 # --- force ---------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("np_,nm,deconv", [(32, 64, 1), (32, 96, 1), (64, 128, 0), (32, 64, 2), (96, 192, 1)])
+@pytest.mark.parametrize("np_,nm,deconv", [(32, 64, 1), (32, 96, 1), (64, 128, 0), (32, 64, 2), (96, 192, 1),
+                                           (64, 32, 1)])
 def test_force_mesh_matches_oracle(C, np_, nm, deconv):
     s = Sim(C, np=np_, nm=nm, box=300.0, deconv=deconv)
     try:
@@ -206,6 +245,37 @@ def test_full_run_cola_32p_64m(C):
         s.close()
 
 
+@pytest.mark.parametrize("np_,nm", [(64, 32), (64, 16)])
+def test_full_run_on_a_coarse_mesh(C, np_, nm):
+    # §7.3's coarse force meshes (N_m = N_p / 2, N_p / 4): the lattice sits at i N_m / N_p + 1/2 cells.
+    kw = workloads.run_params("cola_32p_64m_256mpc", np=np_, nm=nm, seed=17)
+    s = Sim(C, **kw)
+    try:
+        C.colapm_make_ics(s.ctx)
+        cell0, off0, _ = s.state()
+        r = oracle_run(s)
+        r.make_ics(17, ocosmo.linear_pk(0.3, 0.7, 0.96, 0.8))
+        d0 = mesh_coords(cell0, off0) * s.box / nm - r.x
+        d0 -= s.box * np.rint(d0 / s.box)
+        assert np.sqrt(np.mean(d0 ** 2)) < 1e-4 * np.sqrt(np.mean(r.displacement() ** 2))
+        C.colapm_step(s.ctx, -1)
+        cell, off, mom = s.state()
+        r.run()
+        d = mesh_coords(cell, off) * s.box / nm - r.x
+        d -= s.box * np.rint(d / s.box)
+        assert np.sqrt(np.mean(d ** 2)) < 1e-4 * np.sqrt(np.mean(r.displacement() ** 2))
+        psi = np.empty((np_ ** 3, 3), np.float32)
+        C.colapm_get_displacement(s.ctx, psi)
+        assert np.sqrt(np.mean((psi - r.displacement()) ** 2)) < 1e-4 * np.sqrt(np.mean(r.displacement() ** 2))
+        k, pk, nmodes = C.colapm_power(s.ctx, 20)
+        kr, pr, nr = opower.power_from_positions(r.x, s.box, np_, nm, 20)
+        assert np.array_equal(nmodes, nr)
+        ok = nr > 0
+        assert np.nanmax(np.abs(pk[ok] / pr[ok] - 1)) < 1e-3
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("nbins,kmin,kmax", [(100, 0.0, 0.0), (37, 0.05, 0.4), (12, 0.0, 2.0)])
 def test_power_on_shared_positions(C, nbins, kmin, kmax):
     np_, nm = 32, 64
@@ -220,6 +290,38 @@ def test_power_on_shared_positions(C, nbins, kmin, kmax):
         assert np.array_equal(nmodes, nr)
         ok = nr > 0
         assert np.max(np.abs(pk[ok] / pr[ok] - 1)) < 1e-4
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("cola_on", [1, 0])
+def test_redshift_space_power_matches_oracle(C, cola_on):
+    # §7.1: positions moved by v_los / (a H) along the line of sight (radial from the box centre, or
+    # plane-parallel), on the GPU's finalized state shared with the oracle.
+    np_, nm, box = 32, 64, 256.0
+    s = Sim(C, np=np_, nm=nm, box=box, seed=31, cola=cola_on)
+    try:
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, -1)
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_power_rsd(s.ctx, -1, 20)               # velocities are final only after finalize
+        assert e.value.code == -6
+        C.colapm_finalize(s.ctx)
+        cell, off, mom = s.state()
+        x = mesh_coords(cell, off) * (box / nm)
+        p = mom.astype(np.float64) * (box / nm)
+        _, pr_real, _ = C.colapm_power(s.ctx, 40)
+        for los in (-1, 0, 2):
+            k, pk, cnt = C.colapm_power_rsd(s.ctx, los, 40)
+            xs = opower.redshift_space(x, p, 1.0, 0.3, box, los)
+            kr, pr, nr = opower.power_from_positions(xs, box, np_, nm, 40)
+            assert np.array_equal(cnt, nr)
+            ok = nr > 0
+            assert np.max(np.abs(pk[ok] / pr[ok] - 1)) < 1e-4, los
+            assert np.max(np.abs(pk[ok] / pr_real[ok] - 1)) > 1e-2      # redshift space differs
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_power_rsd(s.ctx, 3, 20)
+        assert e.value.code == -1
     finally:
         s.close()
 

@@ -204,7 +204,9 @@ def test_uniform_lattice_has_zero_contrast_at_mesh_ratio_two():
     # The Lagrangian lattice sits half a PM cell off the mesh nodes. With N_m = 2 N_p each particle
     # splits equally over 8 cells and every cell receives exactly 1/8 of one particle, so the mass
     # per cell times the particle mass (N_m/N_p)^3 = 8 cells is exactly the mean: delta = 0 everywhere.
-    for np_, nm in ((8, 16), (4, 4)):
+    # The same holds on the coarse meshes of §7.3 (N_m = N_p / 2, N_p / 4): 8 and 64 particles' worth
+    # of weight per cell, each particle of mass 1/8 and 1/64 cells.
+    for np_, nm in ((8, 16), (4, 4), (16, 8), (16, 4)):
         q = ics.lagrangian_grid(np_, BOX, nm)
         rho = pm.cic_deposit(q * (nm / BOX), nm)
         assert np.all(rho == rho.flat[0]) and rho.sum() == np_ ** 3 << 45
@@ -491,3 +493,107 @@ def test_numpy_fft_primitive_gives_the_same_run():
     pa = power.power_from_positions(a.x, 64.0, 8, 16, 8)
     pb = power.power_from_positions(b.x, 64.0, 8, 16, 8, fft="numpy")
     assert np.allclose(pa[1], pb[1], rtol=1e-9, equal_nan=True)
+
+
+# --- Redshift space (§7.1) --------------------------------------------------------------------------
+
+def test_redshift_space_displacement_by_hand():
+    # Observer at the box centre, particle at centre + (3, 4, 0) Mpc/h, peculiar velocity (500, 0, 0) km/s
+    # at a = 0.5: v_los = 300 km/s along (0.6, 0.8, 0); H(a) = 100 E(a) km/s per Mpc/h; the particle
+    # moves by v_los / (a H) along the line of sight. Momenta in the method's units: v = 100 p / a km/s.
+    box, a, om = 100.0, 0.5, 0.3
+    x = np.array([[53.0, 54.0, 50.0]])
+    p = np.array([[500.0 * a / 100.0, 0.0, 0.0]])
+    h_kms = 100.0 * math.sqrt(om / a ** 3 + 1 - om)
+    shift = 300.0 / (a * h_kms)
+    s = power.redshift_space(x, p, a, om, box)
+    assert np.abs(s[0] - (x[0] + shift * np.array([0.6, 0.8, 0.0]))).max() < 1e-12
+    # plane-parallel along y: the x velocity does not move it; along x it moves by 500 / (a H)
+    assert np.abs(power.redshift_space(x, p, a, om, box, los=1) - x).max() < 1e-12
+    sx = power.redshift_space(x, p, a, om, box, los=0)
+    assert abs(sx[0, 0] - (53.0 + 500.0 / (a * h_kms))) < 1e-12
+    # periodic wrap, and no motion without velocity
+    xe = np.array([[99.9, 1.0, 2.0]])
+    assert power.redshift_space(xe, np.array([[1.0, 0, 0]]), a, om, box, los=0)[0, 0] < 5.0
+    assert np.array_equal(power.redshift_space(x, 0 * p, a, om, box), x)
+
+
+def test_redshift_space_kaiser_factor_in_the_linear_regime():
+    # Zel'dovich particles (Psi2 = 0) at z = 49 with the growing-mode momentum p = P1 Psi1: along the
+    # axis the redshift-space displacement is D1 (Psi + f Psi_z z^), so every low-k mode of the density
+    # is multiplied by 1 + f mu^2 (Kaiser 1987), f = dln D1 / dln a = P1 / (a^3 E D1 / a) (§7.1).
+    n, box, om = 32, 256.0, 0.3
+    a = 0.02
+    d1, _, p1, _ = cosmology.growth(np.array([a]), om)
+    f = p1[0] / (a ** 2 * cosmology.hubble_e(a, om) * d1[0])
+    pk = cosmology.linear_pk(om, 0.7, 0.96, 0.8)
+    dk = ics.gaussian_field(n, box, 21, pk)
+    psi1, _ = ics.lpt_displacements(dk, box)
+    q = ics.lagrangian_grid(n, box, n)
+    psi = ics.per_particle(psi1)
+    x = np.mod(q + d1[0] * psi, box)
+    s = power.redshift_space(x, p1[0] * psi, a, om, box, los=2)
+    dr = fft.fftn(pm.density_contrast(pm.cic_deposit(x * n / box, n), n, n))
+    ds = fft.fftn(pm.density_contrast(pm.cic_deposit(s * n / box, n), n, n))
+    kx, ky, kz, nyq = ics.wavevectors(n, box)
+    k = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    sel = (k > 0) & (k < 4 * 2 * math.pi / box) & ~nyq
+    mu2 = kz[sel] ** 2 / k[sel] ** 2
+    ratio = (ds[sel] / dr[sel]).real
+    assert abs(f - 1.0) < 0.01                       # matter dominated at z = 49
+    assert np.abs(ratio - (1 + f * mu2)).max() < 0.02
+
+
+# --- Local primordial non-Gaussianity (§5) -----------------------------------------------------------
+
+def _d_md(om):
+    return cosmology.growth_matter_era(om)
+
+
+def test_matter_era_growth_normalisation():
+    # EdS: D1 = a exactly; LCDM: within 1% of the Carroll, Press & Turner (1992) fit
+    # g = 5/2 Om / (Om^(4/7) - OL + (1 + Om/2)(1 + OL/70)).
+    assert abs(cosmology.growth_matter_era(1.0) - 1.0) < 1e-10
+    for om in (0.25, 0.3, 0.5):
+        ol = 1 - om
+        cpt = 2.5 * om / (om ** (4 / 7) - ol + (1 + om / 2) * (1 + ol / 70))
+        assert abs(cosmology.growth_matter_era(om) / cpt - 1) < 1e-2
+
+
+def test_fnl_zero_is_the_gaussian_field_and_the_change_is_linear_in_fnl():
+    n, om, h = 16, 0.3, 0.7
+    pk = cosmology.linear_pk(om, h, 0.96, 0.8)
+    dk = ics.gaussian_field(n, BOX, 5, pk)
+    dmd = _d_md(om)
+    d0 = ics.local_fnl_field(dk, BOX, 0.0, om, h, dmd)
+    assert np.abs(d0 - dk).max() < 1e-12 * np.abs(dk).max()
+    d1 = ics.local_fnl_field(dk, BOX, 100.0, om, h, dmd)
+    d2 = ics.local_fnl_field(dk, BOX, 200.0, om, h, dmd)
+    assert np.abs(d1 - dk).max() > 1e-6 * np.abs(dk).max()          # it does something
+    assert np.abs((d2 - dk) - 2 * (d1 - dk)).max() < 1e-9 * np.abs(d1 - dk).max()
+    # the change is f_NL M FFT(phi^2) on every mode but k = 0: the square of the real-space potential
+    m = ics.potential_to_density(n, BOX, om, h, dmd)
+    phi_k = np.where(m > 0, dk / np.where(m > 0, m, 1.0), 0.0)
+    phi = fft.ifftn(phi_k).real
+    sq = m * fft.fftn(phi * phi)
+    _, _, _, nyq = ics.wavevectors(n, BOX)
+    sq[nyq] = 0.0
+    assert np.abs((d1 - dk) - 100.0 * sq).max() < 1e-9 * np.abs(sq).max() * 100.0
+
+
+def test_primordial_potential_amplitude_is_physical():
+    # With sigma_8 = 0.8, the potential implied by M(k) has the order of the observed primordial
+    # curvature amplitude: P_Phi k^3 / (2 pi^2) = (9/25) A_s (k / k_*)^(n_s - 1) at k_* = 0.05 / Mpc
+    # (Phi = 3/5 zeta in matter domination), A_s ~ 2.1e-9 from CMB fits with CAMB spectra. BBKS without
+    # baryons has about 1.5x more power than such spectra where sigma_8 is fixed (k ~ 0.1-0.3 h/Mpc),
+    # so the same sigma_8 implies about half of that A_s (9.5e-10 here). The window rejects a dropped
+    # 2/3 (4.2e-10), a dropped 1/Om (1e-8) or a dropped growth to z = 0 (5.8e-10).
+    om, h, ns = 0.3, 0.7, 0.96
+    pk = cosmology.linear_pk(om, h, ns, 0.8)
+    kstar = 0.05 / h                                            # h/Mpc
+    k = np.array([kstar])
+    t = cosmology.t_bbks(k, om, h)[0]
+    m = 2.0 / 3.0 * (kstar * ics.HUBBLE_DISTANCE) ** 2 * t * _d_md(om) / om
+    p_phi = pk(k)[0] / m ** 2
+    a_s = p_phi * kstar ** 3 / (2 * math.pi ** 2) * 25.0 / 9.0
+    assert 7e-10 < a_s < 2.5e-9, a_s
