@@ -130,6 +130,44 @@ int colapm_finalize(colapm_ctx* ctx);
 int colapm_power(colapm_ctx* ctx, int nbins, double kmin, double kmax,
                  double* k_out, double* p_out, long long* nmodes_out);
 
+/* ---- past lightcone (§6) ------------------------------------------------------------------- */
+/* An observer at `origin` (Mpc/h) sees the past lightcone shrink to it: its radius at scale factor a
+ * is the comoving distance R_L(a) = c int_a^1 da' / (a'^2 H(a')). The box is replicated: every
+ * particle has images x + R L for integer vectors R with rep_lo <= R <= rep_hi per axis. From the
+ * first step boundary at or after a(z_max), the drift of every step records each image that leaves
+ * the lightcone during it (R_p <= R_L at a_i and R_p > R_L at a_{i+1}, R_p its distance to the
+ * observer): its exit time a_L interpolates both radii linearly across the step
+ * (Eq. eq:lightconeinterp), its position is the one the step's drift gives at a_L (Eq. eq:rcola
+ * with every coefficient over [a_i, a_L]), and its momentum is the step's residual momentum (at
+ * a_{i+1/2}, not interpolated, as in the paper) plus, for COLA, the LPT frame momentum at a_L. */
+typedef struct {
+    double origin[3];          /* observer position, Mpc/h                                      */
+    double z_max;              /* redshift at which the lightcone starts (> z_final)            */
+    int rep_lo[3], rep_hi[3];  /* replicate ranges per axis (at most 33 replicates per axis)    */
+} colapm_lightcone;
+
+/* One particle image leaving the lightcone: position (replicated box coordinates, Mpc/h), exit scale
+ * factor, total momentum p = a^3 E dx/da (Mpc/h; velocity in km/s = 100 p / a) and particle id. */
+typedef struct {
+    float x, y, z, a;
+    float px, py, pz;
+    int id;
+} colapm_lc_particle;
+
+/* Turn the lightcone on for the steps that follow (NULL: off), with room for `capacity` output rows
+ * on the device (allocated here; COLAPM_E_NOMEM if that fails). colapm_make_ics starts a new
+ * lightcone (the row count returns to zero). COLAPM_E_ARG for capacity < 1, z_max <= z_final, a
+ * lightcone that starts after the last step, or bad replicate ranges. Synchronises. */
+int colapm_set_lightcone(colapm_ctx* ctx, const colapm_lightcone* lc, long long capacity);
+
+/* The rows recorded so far: *count receives their number; up to max_rows of them (at most the
+ * capacity) are copied to `rows` (host or device, caller-owned; may be NULL when max_rows is 0), in
+ * no particular order, and *copied (may be NULL) how many were. Returns COLAPM_E_OVERFLOW when more
+ * rows were recorded than the capacity holds (the extra rows are lost, *count still counts them; the
+ * stored ones are copied), COLAPM_E_STATE when no lightcone is set. Synchronises. */
+int colapm_get_lightcone(colapm_ctx* ctx, long long* count, colapm_lc_particle* rows, long long max_rows,
+                         long long* copied);
+
 /* §7.1: power spectrum in redshift space. Every particle is moved along the line of sight by
  * s_los = v_los / (H(a) a), v the total peculiar velocity at a_N (the run must be finalized:
  * COLAPM_E_STATE otherwise), the line of sight radial from an observer at the centre of the box
@@ -256,8 +294,8 @@ int colapm_autotune(colapm_ctx* ctx, int* choice);
  * COLAPM_E_ARG otherwise. All engines compute the same transforms and agree to FP32 rounding. */
 int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
 
-/* Reorder the particle arrays by mesh cell before every `every`-th step (0: never, the default
- * unless colapm_autotune chose otherwise). The analogue of the paper's particle migration (§4),
+/* Reorder the particle arrays by mesh cell before every `every`-th step (0: never). The default is
+ * once, halfway through the run (every = n_steps / 2) on meshes of 512^3 cells and more, else never. The analogue of the paper's particle migration (§4),
  * which keeps each rank's particles with its slab of the mesh: here it keeps a warp's particles
  * on neighbouring mesh cells, so that the deposit and the gather read and write runs of cells as
  * structure grows. It is a counting sort of all particle arrays by bucket (z, y, x / 64) of the

@@ -24,6 +24,13 @@ import numpy as np
 from . import cosmology, ics, pm
 
 
+def wrap(x, box):
+    """Periodic wrap into [0, L): np.mod returns L itself for tiny negative x, which is mapped to 0."""
+    x = np.mod(x, box)
+    x[x >= box] -= box
+    return x
+
+
 class Run:
     """State of one simulation in the oracle (all FP64, particle-id order)."""
 
@@ -33,6 +40,7 @@ class Run:
         self.fft = fft
         self.box, self.np_, self.nm = float(box), int(np_), int(nm)
         self.om, self.cola, self.deconv = float(om), bool(cola), int(deconv)
+        self.stepping, self.nlpt = stepping, nlpt
         self.table = cosmology.timestep_table(om, z_init, z_final, n_steps, spacing, stepping, nlpt)
         self.n_steps = int(n_steps)
         self.step_index = 0
@@ -45,7 +53,7 @@ class Run:
         self.q = ics.lagrangian_grid(self.np_, self.box, self.nm)
         self.psi1 = ics.per_particle(psi1)
         self.psi2 = ics.per_particle(psi2)
-        self.x = np.mod(self.q + t["D1"][0] * self.psi1 + t["D2"][0] * self.psi2, self.box)
+        self.x = wrap(self.q + t["D1"][0] * self.psi1 + t["D2"][0] * self.psi2, self.box)
         if self.cola:
             self.p = np.zeros_like(self.x)
         else:
@@ -76,7 +84,7 @@ class Run:
         dx = t["drift"][i] * self.p
         if self.cola:
             dx = dx + t["dD1"][i] * self.psi1 + t["dD2"][i] * self.psi2
-        self.x = np.mod(self.x + dx, self.box)
+        self.x = wrap(self.x + dx, self.box)
         self.step_index += 1
         return force
 

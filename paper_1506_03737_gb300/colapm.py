@@ -39,6 +39,15 @@ class NNConfig(ctypes.Structure):
                 ("engine", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
+class Lightcone(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("z_max", ctypes.c_double), ("rep_lo", ctypes.c_int * 3),
+                ("rep_hi", ctypes.c_int * 3)]
+
+
+# rows of colapm_get_lightcone (colapm_lc_particle)
+LC_DTYPE = np.dtype([("x", np.float32), ("y", np.float32), ("z", np.float32), ("a", np.float32),
+                     ("px", np.float32), ("py", np.float32), ("pz", np.float32), ("id", np.int32)])
+
 NN_PARAMS = 16467
 
 
@@ -59,6 +68,8 @@ def _load():
         "colapm_cross_correlation": (I, [P, P, I, D, D, P, P, P]),
         "colapm_power_rsd": (I, [P, I, I, D, D, P, P, P]),
         "colapm_set_fnl": (I, [P, D]),
+        "colapm_set_lightcone": (I, [P, P, ctypes.c_longlong]),
+        "colapm_get_lightcone": (I, [P, P, P, ctypes.c_longlong, P]),
         "colapm_get_particles": (I, [P, P, P]),
         "colapm_get_particles_async": (I, [P, P, P]),
         "colapm_wait_particles": (I, [P]),
@@ -178,6 +189,34 @@ def colapm_power(ctx, nbins, kmin=0.0, kmax=0.0, k_out=None, p_out=None, n_out=N
     n_out = np.empty(nbins, dtype=np.int64) if n_out is None else n_out
     _check(LIB.colapm_power(ctx, nbins, kmin, kmax, _ptr(k_out), _ptr(p_out), _ptr(n_out)), "colapm_power")
     return k_out, p_out, n_out
+
+
+def colapm_set_lightcone(ctx, origin=None, z_max=1.0, rep_lo=(0, 0, 0), rep_hi=(0, 0, 0), capacity=0):
+    """origin None turns the lightcone off."""
+    if origin is None:
+        _check(LIB.colapm_set_lightcone(ctx, None, 0), "colapm_set_lightcone")
+        return
+    lc = Lightcone()
+    for j in range(3):
+        lc.origin[j] = float(origin[j])
+        lc.rep_lo[j] = int(rep_lo[j])
+        lc.rep_hi[j] = int(rep_hi[j])
+    lc.z_max = float(z_max)
+    _check(LIB.colapm_set_lightcone(ctx, ctypes.byref(lc), int(capacity)), "colapm_set_lightcone")
+
+
+def colapm_get_lightcone(ctx, max_rows=None):
+    """(count, rows): rows is a numpy structured array (LC_DTYPE) of the stored rows; raises
+    ColapmError (code -4) when rows were lost to the capacity."""
+    count, copied = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    code = LIB.colapm_get_lightcone(ctx, ctypes.byref(count), None, 0, None)
+    if code not in (0, -4):
+        _check(code, "colapm_get_lightcone")
+    n = count.value if max_rows is None else min(count.value, max_rows)
+    rows = np.empty(n, dtype=LC_DTYPE)
+    _check(LIB.colapm_get_lightcone(ctx, ctypes.byref(count), rows.ctypes.data_as(ctypes.c_void_p), n,
+                                    ctypes.byref(copied)), "colapm_get_lightcone")
+    return count.value, rows[:copied.value]
 
 
 def colapm_set_fnl(ctx, fnl):

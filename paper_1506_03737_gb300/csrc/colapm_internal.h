@@ -98,12 +98,27 @@ cudaError_t launch_xy_inv(int nm, float2* data, size_t fstride, int nfields, con
 cudaError_t launch_fz(int n_mesh, int mode, float2* in, ZOut out, const float2* tw, const float* sinc2,
                       int deconv, float gnorm, const PowerArgs* pw, cudaStream_t s, bool two_stage = true, bool blocked = false);
 
+// What the drift of one step needs to record the particle images that leave the past lightcone
+// during it (§6). Rows are two float4: (x, y, z, a_L) and (px, py, pz, id bits), Mpc/h.
+struct LightconeStep {
+    float4* out;
+    unsigned long long* count;
+    unsigned long long capacity;
+    const float* tab;        // K samples over [a_i, a_{i+1}], 5 floats each: S, D1 - D1(a_i), D2 - D2(a_i), P1, P2
+    const int* reps;         // 3 * nrep replicate vectors
+    const int* id;           // particle id of each slot (null: slot order is id order)
+    int nrep, K, pad0, pad1;
+    float ox, oy, oz;        // observer, Mpc/h
+    float cell, box;         // cell size and box side, Mpc/h
+    float a0, da, rl0, rl1;  // step start and width; lightcone radius at both ends, Mpc/h
+};
+
 // --- launchers (pm_kernels.cu) --------------------------------------------------------------
 cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s,
                            int block = 256);
 cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1, const float* psi2,
                                      const float* force, size_t np3, int nm, StepCoef c, int drift,
-                                     cudaStream_t s, int block = 256);
+                                     cudaStream_t s, int block = 256, const LightconeStep* lc = nullptr);
 cudaError_t launch_init_particles(float4* pos, float* mom, float* psi1, float* psi2, int np, int nm,
                                   float to_mesh, float d1, float d2, float p1, float p2, int cola,
                                   cudaStream_t s);

@@ -85,7 +85,12 @@ static double kick_coef(double lo, double hi, double af, double om, int stepping
     return 1.5 * om * k;
 }
 
-static double drift_coef(double a0, double a1, double am, double om, int stepping, double n) {
+double comoving_distance(double a, double om) {
+    if (a >= 1.0) return 0.0;
+    return 2997.92458 * integrate([om](double x) { return 1.0 / (x * x * hubble(x, om)); }, a, 1.0, 1024);
+}
+
+double drift_coef(double a0, double a1, double am, double om, int stepping, double n) {
     if (stepping == 1) return integrate([om](double x) { return 1.0 / (x * x * x * hubble(x, om)); }, a0, a1);
     return std::pow(am, -n) * integrate([om, n](double x) { return std::pow(x, n - 3.0) / hubble(x, om); }, a0, a1);
 }
@@ -114,13 +119,13 @@ StepTable make_step_table(double om, double z_init, double z_final, int n_steps,
     return t;
 }
 
-// BBKS transfer function, q = k / (Om h).
 double growth_matter_era(double om) {
     double y[4];
     growth_raw(1.0, om, y);
     return y[0];   // D1(1) with D1 = a deep in matter domination
 }
 
+// BBKS transfer function, q = k / (Om h).
 double bbks(double k, double om, double h) {
     const double q = k / (om * h);
     if (q < 1e-12) return 1.0;

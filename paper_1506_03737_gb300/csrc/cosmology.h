@@ -15,6 +15,13 @@ Growth growth_at(double a, double om);
 // density from the matter era to z = 0).
 double growth_matter_era(double om);
 
+// Drift coefficient over [a0, a1] with the momentum taken at am (§2.3): Quinn (stepping 1) or
+// modified with n = nLPT (stepping 0).
+double drift_coef(double a0, double a1, double am, double om, int stepping, double n);
+
+// Comoving distance to scale factor a, R_L(a) = (c / H0) int_a^1 da' / (a'^2 E(a')), Mpc/h (§6).
+double comoving_distance(double a, double om);
+
 // BBKS (1986) transfer function, Gamma = om h, k in h/Mpc.
 double bbks(double k, double om, double h);
 

@@ -27,7 +27,7 @@ static cudaError_t fz2(float2* in, ZOut out, const float2* tw, const float* sinc
 template <int N, int MODE>
 static cudaError_t fz_mode(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm,
                            PowerArgs pw, cudaStream_t s, bool two_stage, bool blocked) {
-    if constexpr (F2Has<N>::value) if (two_stage) {
+    if constexpr (F2Has<N>::value && MODE != Z_SCALE_FWD && MODE != Z_SCALE_INV) if (two_stage) {
         if constexpr (MODE == Z_FORCE || MODE == Z_POWER) {
             if (blocked) return fz2<N, MODE, true>(in, out, tw, sinc2, deconv, gnorm, pw, s);
         } else {
@@ -57,6 +57,8 @@ static cudaError_t fz_t(int mode, float2* in, ZOut out, const float2* tw, const 
         case Z_LPT1: return fz_mode<N, Z_LPT1>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts, blk);
         case Z_LPT2: return fz_mode<N, Z_LPT2>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts, blk);
         case Z_POWER: return fz_mode<N, Z_POWER>(in, out, tw, sinc2, deconv, gnorm, pw, s, ts, blk);
+        case Z_SCALE_FWD: return fz_mode<N, Z_SCALE_FWD>(in, out, tw, sinc2, deconv, gnorm, pw, s, false, blk);
+        case Z_SCALE_INV: return fz_mode<N, Z_SCALE_INV>(in, out, tw, sinc2, deconv, gnorm, pw, s, false, blk);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -60,9 +60,59 @@ __global__ void k_deposit(const float4* __restrict__ pos, size_t np3, int nm, un
         }
 }
 
+// Records the images of one particle that leave the past lightcone during the drift (§6): the image
+// x + R L (R in the step's replicate list) leaves when R_p <= R_L at a_i and R_p > R_L at a_{i+1};
+// its exit time interpolates both radii linearly (Eq. eq:lightconeinterp) and it is written at the
+// position the drift gives at a_L, with the residual momentum of the step plus the LPT frame momentum
+// at a_L (the host fills zeros for the LPT columns of plain PM). Units: Mpc/h.
+__device__ __forceinline__ void record_lightcone(const LightconeStep& lc, const int* cell, const float* off,
+                                                 const float* d, const float* v, const float* s1, const float* s2,
+                                                 size_t p) {
+    float xi[3], xn[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        xi[j] = ((float)cell[j] + off[j]) * lc.cell;
+        xn[j] = xi[j] + d[j] * lc.cell;   // unwrapped: the image's path is continuous within the step
+    }
+    const float o[3] = {lc.ox, lc.oy, lc.oz};
+    for (int r = 0; r < lc.nrep; ++r) {
+        float q0 = 0.0f, q1 = 0.0f, sh[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            sh[j] = (float)lc.reps[3 * r + j] * lc.box - o[j];
+            const float u0 = xi[j] + sh[j], u1 = xn[j] + sh[j];
+            q0 = fmaf(u0, u0, q0);
+            q1 = fmaf(u1, u1, q1);
+        }
+        const float rp0 = sqrtf(q0), rp1 = sqrtf(q1);
+        if (!(rp0 <= lc.rl0 && rp1 > lc.rl1)) continue;
+        const float aL = lc.a0 + lc.da * (lc.rl0 - rp0) / ((rp1 - rp0) - (lc.rl1 - lc.rl0));
+        float f = (aL - lc.a0) / lc.da * (float)(lc.K - 1);
+        f = fminf(fmaxf(f, 0.0f), (float)(lc.K - 1));
+        const int k = min((int)f, lc.K - 2);
+        const float w = f - (float)k;
+        float c[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) c[m] = fmaf(w, lc.tab[5 * (k + 1) + m] - lc.tab[5 * k + m], lc.tab[5 * k + m]);
+        float x[3], pm[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            x[j] = xi[j] + sh[j] + o[j] + lc.cell * fmaf(c[0], v[j], fmaf(c[1], s1[j], c[2] * s2[j]));
+            pm[j] = lc.cell * fmaf(c[3], s1[j], fmaf(c[4], s2[j], v[j]));
+        }
+        const unsigned long long slot = atomicAdd(lc.count, 1ull);
+        if (slot < lc.capacity) {
+            const int id = lc.id ? lc.id[p] : (int)p;
+            lc.out[2 * slot] = make_float4(x[0], x[1], x[2], aL);
+            lc.out[2 * slot + 1] = make_float4(pm[0], pm[1], pm[2], __int_as_float(id));
+        }
+    }
+}
+
+template <bool LC>
 __global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict__ mom, const float* __restrict__ psi1,
                                     const float* __restrict__ psi2, const float* __restrict__ force, size_t np3, int nm,
-                                    StepCoef k, int drift) {
+                                    StepCoef k, int drift, LightconeStep lc) {
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
     // every load of the particle's own data is issued before the force loads that depend on its
@@ -110,6 +160,7 @@ __global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict_
         d[j] = drift ? fmaf(k.drift, v[j], fmaf(k.e1, s1[j], k.e2 * s2[j])) : 0.0f;
     }
     if (!drift) return;
+    if constexpr (LC) record_lightcone(lc, cell, off, d, v, s1, s2, p);
     float o[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -362,8 +413,13 @@ cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long 
 }
 
 cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1, const float* psi2, const float* force,
-                                     size_t np3, int nm, StepCoef c, int drift, cudaStream_t s, int block) {
-    k_gather_kick_drift<<<blocks(np3, block), block, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift);
+                                     size_t np3, int nm, StepCoef c, int drift, cudaStream_t s, int block,
+                                     const LightconeStep* lc) {
+    if (lc && drift)
+        k_gather_kick_drift<true><<<blocks(np3, block), block, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift, *lc);
+    else
+        k_gather_kick_drift<false><<<blocks(np3, block), block, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift,
+                                                                        LightconeStep{});
     return cudaGetLastError();
 }
 

@@ -577,3 +577,71 @@ def test_async_catalogue_copy_matches_sync(C):
     finally:
         s.close()
 
+
+
+# --- past lightcone (§6) ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("sort_every,cola_on", [(0, 1), (3, 1), (0, 0)])
+def test_lightcone_matches_oracle(C, sort_every, cola_on):
+    from oracle import lightcone as olc
+    np_, nm, box = 16, 32, 256.0
+    origin, z_max, lo, hi = (30.0, 128.0, 200.0), 0.3, (-1, -1, 0), (1, 1, 1)
+    s = Sim(C, np=np_, nm=nm, box=box, seed=3, cola=cola_on)
+    try:
+        C.colapm_set_sort(s.ctx, sort_every)
+        C.colapm_set_lightcone(s.ctx, origin, z_max, lo, hi, capacity=200000)
+        C.colapm_make_ics(s.ctx)
+        g1, g2 = s.lpt()
+        C.colapm_step(s.ctx, -1)
+        count, rows = C.colapm_get_lightcone(s.ctx)
+        assert count == len(rows) > 500
+        r = olc.LightconeRun(box, np_, nm, 0.3, 9.0, 0.0, 10, cola=bool(cola_on), origin=origin, z_max=z_max,
+                             rep_lo=lo, rep_hi=hi)
+        r.set_displacements(g1.astype(np.float64), g2.astype(np.float64))
+        r.run()
+        ref = r.lightcone()
+        # pair the rows of every particle by position; all but a handful of marginal exits agree
+        by_id = {}
+        for row in ref:
+            by_id.setdefault(int(row[7]), []).append(row)
+        matched, dpos, da, dmom = 0, [], [], []
+        for g in rows:
+            cand = by_id.get(int(g["id"]), [])
+            if not cand:
+                continue
+            gp = np.array([g["x"], g["y"], g["z"]], np.float64)
+            k = int(np.argmin([np.linalg.norm(c[:3] - gp) for c in cand]))
+            c = cand.pop(k)
+            matched += 1
+            dpos.append(np.linalg.norm(c[:3] - gp))
+            da.append(abs(c[3] - g["a"]))
+            dmom.append(np.linalg.norm(c[4:7] - [g["px"], g["py"], g["pz"]]) / max(np.linalg.norm(c[4:7]), 1e-3))
+        assert len(ref) - matched <= 3 and len(rows) - matched <= 3
+        assert np.max(dpos) < 2e-2 and np.median(dpos) < 2e-3      # Mpc/h
+        assert np.max(da) < 1e-5
+        assert np.median(dmom) < 1e-4
+        # a new realisation starts a new lightcone
+        C.colapm_make_ics(s.ctx)
+        assert C.colapm_get_lightcone(s.ctx)[0] == 0
+    finally:
+        s.close()
+
+
+def test_lightcone_capacity_and_arguments(C):
+    s = Sim(C, np=16, nm=32, box=256.0, seed=3)
+    try:
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_get_lightcone(s.ctx)                              # none set
+        assert e.value.code == -6
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_set_lightcone(s.ctx, (0, 0, 0), -0.5, capacity=10)   # starts after z_final
+        assert e.value.code == -1
+        C.colapm_set_lightcone(s.ctx, (128.0, 128.0, 128.0), 0.5, (-1, -1, -1), (1, 1, 1), capacity=50)
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, -1)
+        with pytest.raises(C.ColapmError) as e:
+            C.colapm_get_lightcone(s.ctx)
+        assert e.value.code == -4                                      # more images than rows
+        C.colapm_set_lightcone(s.ctx, None)
+    finally:
+        s.close()

@@ -9,6 +9,8 @@ import math
 import numpy as np
 import pytest
 
+from scipy import integrate
+
 from oracle import cola, cosmology, fft, ics, pm, power
 
 BOX = 256.0
@@ -597,3 +599,90 @@ def test_primordial_potential_amplitude_is_physical():
     p_phi = pk(k)[0] / m ** 2
     a_s = p_phi * kstar ** 3 / (2 * math.pi ** 2) * 25.0 / 9.0
     assert 7e-10 < a_s < 2.5e-9, a_s
+
+
+# --- Lightcone (§6) ------------------------------------------------------------------------------------
+
+def test_comoving_distance_eds_closed_form():
+    from oracle import lightcone
+    # EdS: int_a^1 da / (a^2 a^-3/2) = 2 (1 - sqrt(a))
+    for a in (0.25, 0.5, 0.9):
+        assert abs(lightcone.comoving_distance(a, 1.0) / (2 * lightcone.HUBBLE_DISTANCE * (1 - math.sqrt(a))) - 1) < 1e-12
+
+
+def _lonely_particle_run(r_obs, stepping="modified", cola_on=True, n_steps=10):
+    """One particle at distance r_obs (Mpc/h) from the observer, no displacement: it feels no force
+    (zero self-force) and stays put, so it leaves the lightcone when R_L(a) = r_obs."""
+    from oracle import lightcone
+    box = 2000.0
+    r = lightcone.LightconeRun(box, 1, 4, 0.3, 9.0, 0.0, n_steps, stepping=stepping, cola=cola_on,
+                               origin=(0.0, 0.0, 0.0), z_max=1.0)
+    r.set_displacements(np.zeros((3, 1, 1, 1)), np.zeros((3, 1, 1, 1)))
+    r.x = np.array([[r_obs, 0.0, 0.0]])
+    r.run()
+    return r
+
+
+def test_lightcone_exit_of_a_particle_at_rest():
+    # The exit time is the interpolation of Eq. eq:lightconeinterp; against the exact root of
+    # R_L(a) = R it is off by the curvature of R_L within the step only (<0.5% in a, as in §6.1.1),
+    # and exact at a step boundary; the output position is the particle's own.
+    from oracle import lightcone
+    from scipy import optimize
+    for r_obs in (500.0, 1234.5, 1900.0):
+        r = _lonely_particle_run(r_obs)
+        out = r.lightcone()
+        assert len(out) == 1
+        exact = optimize.brentq(lambda a: lightcone.comoving_distance(a, 0.3) - r_obs, 0.3, 1.0, xtol=1e-14)
+        assert abs(out[0, 3] / exact - 1) < 5e-3
+        assert np.abs(out[0, :3] - [r_obs, 0, 0]).max() < 1e-9
+    a = r.table["a"]
+    rl = lightcone.comoving_distance(a[6], 0.3)
+    out = _lonely_particle_run(rl * (1 - 1e-12)).lightcone()
+    assert abs(out[0, 3] - a[6]) < 1e-9
+
+
+def test_lightcone_drift_to_the_exit_time():
+    # Plain PM, one particle with constant momentum (no force): between boundaries it moves by
+    # p int_{a_i}^{a_L} da / (a^3 E) (Quinn drift, Eq. 16 at a_L); the output lies on that path and on
+    # the interpolated radius.
+    from oracle import lightcone
+    r = lightcone.LightconeRun(3000.0, 1, 4, 0.3, 9.0, 0.0, 10, stepping="quinn", cola=False,
+                               origin=(0.0, 0.0, 0.0), z_max=2.0)
+    r.set_displacements(np.zeros((3, 1, 1, 1)), np.zeros((3, 1, 1, 1)))
+    x0 = np.array([1500.0, 300.0, 200.0])
+    r.x = x0[None, :].copy()
+    r.p = np.array([[-200.0, 50.0, 0.0]])
+    a = r.table["a"]
+    r.run()
+    out = r.lightcone()
+    assert len(out) == 1
+    al = out[0, 3]
+    i = int(np.searchsorted(a, al)) - 1
+    xi = x0 + r.p[0] * sum(cosmology.drift_coeff(a[j], a[j + 1], 0.0, 0.3, "quinn") for j in range(i))
+    s, _ = integrate.quad(lambda v: 1.0 / (v ** 3 * cosmology.hubble_e(v, 0.3)), a[i], al, epsrel=1e-13)
+    assert np.abs(out[0, :3] - (xi + r.p[0] * s)).max() < 1e-8 * np.abs(xi).max()
+    assert np.abs(out[0, 4:7] - r.p[0]).max() < 1e-12
+
+
+def test_every_image_inside_the_start_radius_leaves_exactly_once():
+    # With z_final = 0 the lightcone shrinks to the observer, so every particle image inside the
+    # lightcone at its start leaves during the run, once; images outside never enter (v << c).
+    from oracle import lightcone
+    pk = cosmology.linear_pk(0.3, 0.7, 0.96, 0.8)
+    box, np_ = 300.0, 8
+    r = lightcone.LightconeRun(box, np_, 16, 0.3, 9.0, 0.0, 8, origin=(20.0, 150.0, 280.0), z_max=0.2,
+                               rep_lo=(-1, -1, 0), rep_hi=(1, 1, 1))
+    r.make_ics(4, pk)
+    r.run(r.first)
+    rl = lightcone.comoving_distance(r.table["a"][r.first], 0.3)
+    inside = 0
+    for rep in r.reps:
+        d = r.x + rep * box - r.origin
+        inside += int(np.sum(np.sqrt(np.sum(d * d, axis=1)) <= rl))
+    r.run()
+    out = r.lightcone()
+    assert inside > 100 and len(out) == inside
+    # one output per (particle, image): the image is the output position minus the drift, within half a box
+    keys = {(int(row[7]), tuple(np.floor((row[:3] - r.x[int(row[7])] + box / 2) / box).astype(int))) for row in out}
+    assert len(keys) == len(out)
