@@ -279,20 +279,45 @@ int colapm_get_timing(colapm_ctx* ctx, double* ms, long long* launches);
 long long colapm_kernel_launches(const colapm_ctx* ctx);
 
 /* ---- autotuning ------------------------------------------------------------------------- */
-/* Time the candidate configurations of this context on its current state -- the FFT engine
- * (fused x-y passes through an L2-resident ring for N_m = 512 and 1024, the two-stage register
- * FFT, or shared-memory Stockham, where each exists) and the block size of
- * the particle kernels (128, 256, 512) -- keep the fastest, and remember it for later contexts
- * with the same (np, nm) in this process. The particle state and step counter are restored.
- * Requires initial conditions (COLAPM_E_STATE). Synchronises. `choice` (may be NULL, else 3 ints)
- * receives {two_stage (0/1), block, fused x-y passes (0 or 3)}. */
+/* The mesh passes of a force computation, each on the two-stage register FFT (bit set) or on the
+ * multi-stage shared-memory Stockham FFT (bit clear). A pass whose line length has no two-stage
+ * plan (the lengths 64, 96, 128, 160, 192, 256, 320, 384, 512, 1024 have one: two radices in
+ * {8, 10, 12, 16, 20, 24, 32}) runs on the Stockham plan either way. The initial-condition
+ * transforms on the particle grid take the same choice per kind of pass. */
+#define COLAPM_PLAN_XF 1u    /* forward x pass (r2c of the density)                  */
+#define COLAPM_PLAN_Y 2u     /* y passes, both directions                             */
+#define COLAPM_PLAN_Z 4u     /* z passes (Poisson operator fused; power spectrum)     */
+#define COLAPM_PLAN_XI 8u    /* inverse x pass (c2r of the forces)                    */
+#define COLAPM_PLAN_ALL 15u  /* the default                                           */
+
+/* Time the candidate configurations of this context on its current state, keep the fastest, and
+ * remember it for later contexts (and batches) with the same (np, nm) in this process:
+ *   1. the FFT engine -- fused x-y passes through an L2-resident ring (N_m = 512 and 1024), every
+ *      pass two-stage, or every pass Stockham -- times the block size of the particle kernels
+ *      (128, 256, 512);
+ *   2. then, unless the fused passes won, the radix plan of each pass (COLAPM_PLAN_* bits) in
+ *      turn: a pass switched to the other plan is kept if the step gets faster.
+ * Each candidate is one force computation and gather from the same state (fastest of three after
+ * a warm-up). The particle state and step counter are restored. Requires initial conditions
+ * (COLAPM_E_STATE). Synchronises. `choice` (may be NULL, else 3 ints) receives {1 if every pass is
+ * two-stage else 0, block, fused x-y passes (0 or 3)}; colapm_get_config gives the whole choice. */
 int colapm_autotune(colapm_ctx* ctx, int* choice);
 
 /* Select the configuration explicitly (e.g. to compare engines or to pin a choice): fused x-y
  * passes as a bit mask (1 forward, 2 inverse, 3 both; default 0; ignored where N_m has none),
- * two-stage register FFT (else Stockham) and the particle-kernel block size (128, 256 or 512);
- * COLAPM_E_ARG otherwise. All engines compute the same transforms and agree to FP32 rounding. */
+ * two-stage register FFT in every pass (else Stockham in every pass) and the particle-kernel
+ * block size (128, 256 or 512); COLAPM_E_ARG otherwise. All engines compute the same transforms
+ * and agree to FP32 rounding. */
 int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
+
+/* Select the plan per pass: a mask of COLAPM_PLAN_* bits (two-stage where set). The blocked
+ * half-spectrum layout of the 512^3 and 1024^3 meshes needs every pass two-stage; any other mask
+ * uses the plain layout there. COLAPM_E_ARG outside 0 ... COLAPM_PLAN_ALL. */
+int colapm_set_plan(colapm_ctx* ctx, int plan);
+
+/* The context's configuration: cfg (4 ints) = {plan mask, particle-kernel block size, fused x-y
+ * passes (0 where N_m has none), sort cadence (colapm_set_sort)}. */
+int colapm_get_config(const colapm_ctx* ctx, int* cfg);
 
 /* Reorder the particle arrays by mesh cell before every `every`-th step (0: never). The default is
  * once, halfway through the run (every = n_steps / 2) on meshes of 512^3 cells and more, else never. The analogue of the paper's particle migration (§4),
@@ -317,12 +342,25 @@ int colapm_batch_create(int n, const colapm_params* ps, int nstreams, void* stre
  * in ps), all n_steps COLA steps, and the P(k) of each mock in nbins bins (kmin/kmax <= 0: the
  * per-mock defaults of colapm_power). The whole batch is captured once into a CUDA graph (per
  * nbins/kmin/kmax) and replayed; seeds reach the graph through a pinned buffer, so each run is
- * a new set of realisations. Outputs are host arrays of n * nbins (mock-major). Synchronises. */
+ * a new set of realisations. Before the first capture, every (np, nm) of the batch without a
+ * tuned configuration in this process is autotuned on its first mock (colapm_autotune) and the
+ * choice given to all mocks of that size. Outputs are host arrays of n * nbins (mock-major).
+ * Synchronises. */
 int colapm_batch_run(colapm_batch* b, const unsigned long long* seeds, int nbins, double kmin, double kmax,
                      double* k_out, double* p_out, long long* nmodes_out);
 
 /* Worker streams in use (after the first run when chosen automatically). */
 int colapm_batch_streams(const colapm_batch* b);
+
+/* Schedule of the batch's steps. on = 1 (the default): lockstep -- the mocks advance one step at a
+ * time together; each step is one multi-mock deposit of every mock still running, the mesh passes
+ * of each mock, and one multi-mock gather-kick-drift. The two multi-mock kernels are persistent:
+ * their CTAs take work items (mock, chunk of 256 particles) from a ticket counter across all the
+ * mocks, whatever their sizes. on = 0: each mock runs its ICs, steps and P(k) in turn (on worker
+ * streams). Both give the same results bit for bit (the per-particle code is the same and the
+ * fixed-point deposit does not depend on order). The next run captures the chosen schedule.
+ * COLAPM_E_ARG for other values. */
+int colapm_batch_set_lockstep(colapm_batch* b, int on);
 
 void colapm_batch_destroy(colapm_batch* b);
 

@@ -16,8 +16,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcolapm.so")
 
-SOURCES = ["colapm.cu", "fft_x.cu", "fft_y.cu", "fft_z.cu", "fft_xy.cu", "pm_kernels.cu", "ics_kernels.cu",
-           "sort_kernels.cu", "cosmology.cpp", "noalloc.cu", "nn.cu"]
+SOURCES = ["colapm.cu", "fft_x.cu", "fft_y.cu", "fft_z.cu", "fft_z_mid.cu", "fft_z_big.cu", "fft_xy.cu",
+           "pm_kernels.cu", "ics_kernels.cu", "sort_kernels.cu", "cosmology.cpp", "noalloc.cu", "nn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 

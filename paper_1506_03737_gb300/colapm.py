@@ -91,10 +91,13 @@ def _load():
         "colapm_power_noalloc": (I, [P, P, ctypes.c_longlong, I, D, I, D, D, P, P, P, P]),
         "colapm_autotune": (I, [P, P]),
         "colapm_set_engine": (I, [P, I, I, I]),
+        "colapm_set_plan": (I, [P, I]),
+        "colapm_get_config": (I, [P, P]),
         "colapm_set_sort": (I, [P, I]),
         "colapm_batch_create": (I, [I, P, I, P, ctypes.POINTER(P)]),
         "colapm_batch_run": (I, [P, P, I, D, D, P, P, P]),
         "colapm_batch_streams": (I, [P]),
+        "colapm_batch_set_lockstep": (I, [P, I]),
         "colapm_batch_destroy": (None, [P]),
         "colapm_get_displacement": (I, [P, P]),
         "colapm_set_displacement": (I, [P, P]),
@@ -332,6 +335,19 @@ def colapm_set_engine(ctx, fused=3, two_stage=True, block=256):
     _check(LIB.colapm_set_engine(ctx, int(fused), int(two_stage), int(block)), "colapm_set_engine")
 
 
+PLAN_XF, PLAN_Y, PLAN_Z, PLAN_XI, PLAN_ALL = 1, 2, 4, 8, 15
+
+
+def colapm_set_plan(ctx, plan):
+    _check(LIB.colapm_set_plan(ctx, int(plan)), "colapm_set_plan")
+
+
+def colapm_get_config(ctx):
+    cfg = np.zeros(4, dtype=np.int32)
+    _check(LIB.colapm_get_config(ctx, _ptr(cfg)), "colapm_get_config")
+    return {"plan": int(cfg[0]), "block": int(cfg[1]), "fused": int(cfg[2]), "sort_every": int(cfg[3])}
+
+
 def colapm_batch_create(params_list, nstreams=0, stream=0):
     arr = (Params * len(params_list))(*params_list)
     b = ctypes.c_void_p()
@@ -351,6 +367,10 @@ def colapm_batch_run(b, n, nbins, seeds=None, kmin=0.0, kmax=0.0):
 
 def colapm_batch_streams(b):
     return LIB.colapm_batch_streams(b)
+
+
+def colapm_batch_set_lockstep(b, on=True):
+    _check(LIB.colapm_batch_set_lockstep(b, int(bool(on))), "colapm_batch_set_lockstep")
 
 
 def colapm_batch_destroy(b):

@@ -68,7 +68,7 @@ struct colapm_ctx {
     int pw_n2cap = 0, pw_nbcap = 0;
     unsigned long long* d_seed = nullptr;          // device seed of the Gaussian field
     const unsigned long long* seed_src = nullptr;  // the seed the ICs read (own, or a batch slot)
-    bool two_stage = true;               // FFT engine for 256/512/1024 lines (autotuned)
+    unsigned plan = COLAPM_PLAN_ALL;     // passes on the two-stage register FFT, else Stockham (autotuned)
     int fused = 0;                       // fused x-y passes where supported: bit 0 forward, bit 1 inverse (autotuned)
     bool rho_clean = false;              // rho is all zero (the forward x pass clears it as it reads)
     int phase_mute = 0;                  // > 0: phases nested in another phase are not timed
@@ -205,9 +205,16 @@ int deposit(colapm_ctx* c, const DepositSrc* src = nullptr) {
 
 bool use_xy(const colapm_ctx* c, int bit) { return (c->fused & bit) && c->xy_ring != nullptr; }
 
-// The two-stage engine keeps the half spectra in the blocked layout (see hs_index) unless the fused
-// x-y passes are selected; the inverse x pass then writes the real force meshes to Freal.
-bool use_blocked(const colapm_ctx* c) { return c->two_stage && !(c->fused & 3) && c->Freal != nullptr; }
+// Whether pass `bit` (COLAPM_PLAN_*) runs on the two-stage register FFT (where its length has a
+// two-radix plan; the launchers fall back to the Stockham plan otherwise).
+bool ts(const colapm_ctx* c, unsigned bit) { return (c->plan & bit) != 0; }
+
+// The two-stage engine keeps the half spectra in the blocked layout (see hs_index) when every pass
+// runs on it and the fused x-y passes are off; the inverse x pass then writes the real force
+// meshes to Freal.
+bool use_blocked(const colapm_ctx* c) {
+    return c->plan == COLAPM_PLAN_ALL && !(c->fused & 3) && c->Freal != nullptr;
+}
 
 // The three real force meshes of the last force computation.
 const float* force_mesh(const colapm_ctx* c) { return use_blocked(c) ? c->Freal : c->F; }
@@ -259,17 +266,16 @@ int density_xy(colapm_ctx* c) {
         return COLAPM_OK;
     }
     const bool blk = use_blocked(c);
-    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, c->two_stage, true, blk));
+    CKL(launch_fx_fwd_i64(c->nm, c->rho, d, c->tw_m, density_scale(c), c->err, c->stream, ts(c, COLAPM_PLAN_XF), true,
+                          blk));
     c->rho_clean = true;
-    CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream, c->two_stage, blk));
+    CKL(launch_fy(c->nm, -1, d, 0, 1, c->tw_m, c->stream, ts(c, COLAPM_PLAN_Y), blk));
     return COLAPM_OK;
 }
 
-// §2.4 steps 1-3: the three real force meshes F_j = -d psi / dx_j (cells) in force_mesh(c).
-int compute_force(colapm_ctx* c) {
-    int r = deposit(c);
-    if (r) return r;
-    r = density_xy(c);
+// §2.4 steps 2-3 from the deposited density: the three real force meshes in force_mesh(c).
+int force_from_density(colapm_ctx* c) {
+    int r = density_xy(c);
     if (r) return r;
     float2* d = reinterpret_cast<float2*>(c->F);
     const size_t fs = c->nm3 / 2;   // complex stride between the three meshes
@@ -280,8 +286,8 @@ int compute_force(colapm_ctx* c) {
         out.p[1] = d + fs;
         out.p[2] = d + 2 * fs;
         const float gnorm = (float)(1.0 / ((double)c->nm * c->nm * c->nm));
-        CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream, c->two_stage,
-                      use_blocked(c)));
+        CKL(launch_fz(c->nm, Z_FORCE, d, out, c->tw_m, c->sinc2_m, c->prm.deconv, gnorm, nullptr, c->stream,
+                      ts(c, COLAPM_PLAN_Z), use_blocked(c)));
     }
     if (use_xy(c, 2)) {
         Phase ph(c, COLAPM_PHASE_FFT_INV);
@@ -294,15 +300,22 @@ int compute_force(colapm_ctx* c) {
         if (blk) {
             CKL(launch_fy_force(c->nm, d, fs, c->tw_m, c->stream));   // bases -> three spectra
         } else {
-            CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk));
+            CKL(launch_fy(c->nm, +1, d, fs, 3, c->tw_m, c->stream, ts(c, COLAPM_PLAN_Y), blk));
         }
     }
     {
         Phase ph(c, COLAPM_PHASE_FFT_INV_X);
-        CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, c->two_stage, blk,
+        CKL(launch_fx_inv(c->nm, d, fs, 3, c->tw_m, c->stream, ts(c, COLAPM_PLAN_XI), blk,
                           blk ? reinterpret_cast<float2*>(c->Freal) : nullptr));
     }
     return COLAPM_OK;
+}
+
+// §2.4 steps 1-3: the three real force meshes F_j = -d psi / dx_j (cells) in force_mesh(c).
+int compute_force(colapm_ctx* c) {
+    int r = deposit(c);
+    if (r) return r;
+    return force_from_density(c);
 }
 
 StepCoef coef_for(const colapm_ctx* c, int i) {
@@ -442,6 +455,19 @@ const char* colapm_strerror(int code) {
     }
 }
 
+}  // extern "C"
+
+// Configurations chosen by colapm_autotune in this process, applied to every later context (and
+// batch mock) of the same size.
+static std::mutex g_tune_mu;
+struct Tuned {
+    unsigned plan;
+    int fused, block;
+};
+static std::map<std::pair<int, int>, Tuned> g_tuned;   // (np, nm) -> choice
+
+extern "C" {
+
 int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
     if (!out) return COLAPM_E_ARG;
     *out = nullptr;
@@ -511,6 +537,15 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
     // 1024^3 one sort before step 5 of 10 measured 28.7 against 29.1 ms per step; more frequent sorts
     // cost more than they save, see colapm_set_sort).
     c->sort_every = c->nm >= 512 && p->n_steps >= 4 ? p->n_steps / 2 : 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find({c->np, c->nm});
+        if (it != g_tuned.end()) {
+            c->plan = it->second.plan;
+            c->fused = it->second.fused;
+            c->block = it->second.block;
+        }
+    }
     *out = c;
     return COLAPM_OK;
 }
@@ -538,20 +573,20 @@ int colapm_make_ics(colapm_ctx* c) {
     ZOut o1{};
     for (int j = 0; j < 3; ++j) o1.p[j] = p1 + j * hs;
     for (int j = 0; j < 6; ++j) o1.p[3 + j] = phi + j * hs;
-    CKL(launch_fz(np, Z_LPT1, dk, o1, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream, c->two_stage));
-    CKL(launch_fy(np, +1, p1, hs, 3, c->tw_p, c->stream, c->two_stage));
-    CKL(launch_fy(np, +1, phi, hs, 6, c->tw_p, c->stream, c->two_stage));
-    CKL(launch_fx_inv(np, p1, hs, 3, c->tw_p, c->stream, c->two_stage));
-    CKL(launch_fx_inv(np, phi, hs, 6, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fz(np, Z_LPT1, dk, o1, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream, ts(c, COLAPM_PLAN_Z)));
+    CKL(launch_fy(np, +1, p1, hs, 3, c->tw_p, c->stream, ts(c, COLAPM_PLAN_Y)));
+    CKL(launch_fy(np, +1, phi, hs, 6, c->tw_p, c->stream, ts(c, COLAPM_PLAN_Y)));
+    CKL(launch_fx_inv(np, p1, hs, 3, c->tw_p, c->stream, ts(c, COLAPM_PLAN_XI)));
+    CKL(launch_fx_inv(np, phi, hs, 6, c->tw_p, c->stream, ts(c, COLAPM_PLAN_XI)));
     // 2LPT: S from the six phi_ij, then Psi2 = -i k S_k / k^2.
     CKL(launch_lpt2_source(c->scratch + np3, np3, c->scratch, c->stream));
-    CKL(launch_fx_fwd_f32(np, c->scratch, phi, c->tw_p, c->stream, c->two_stage));
-    CKL(launch_fy(np, -1, phi, 0, 1, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fx_fwd_f32(np, c->scratch, phi, c->tw_p, c->stream, ts(c, COLAPM_PLAN_XF)));
+    CKL(launch_fy(np, -1, phi, 0, 1, c->tw_p, c->stream, ts(c, COLAPM_PLAN_Y)));
     ZOut o2{};
     for (int j = 0; j < 3; ++j) o2.p[j] = p2 + j * hs;
-    CKL(launch_fz(np, Z_LPT2, phi, o2, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream, c->two_stage));
-    CKL(launch_fy(np, +1, p2, hs, 3, c->tw_p, c->stream, c->two_stage));
-    CKL(launch_fx_inv(np, p2, hs, 3, c->tw_p, c->stream, c->two_stage));
+    CKL(launch_fz(np, Z_LPT2, phi, o2, c->tw_p, nullptr, 0, gnorm, nullptr, c->stream, ts(c, COLAPM_PLAN_Z)));
+    CKL(launch_fy(np, +1, p2, hs, 3, c->tw_p, c->stream, ts(c, COLAPM_PLAN_Y)));
+    CKL(launch_fx_inv(np, p2, hs, 3, c->tw_p, c->stream, ts(c, COLAPM_PLAN_XI)));
     return place_particles(c, (float)c->nm / np);
 }
 
@@ -688,7 +723,7 @@ int power_enqueue(colapm_ctx* c, int nbins, const DepositSrc* src = nullptr, boo
     const double nm = c->nm;
     pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
     CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m + (window ? 0 : c->nm), 0, 1.0f, &pw,
-                  c->stream, c->two_stage, use_blocked(c)));
+                  c->stream, ts(c, COLAPM_PLAN_Z), use_blocked(c)));
     return COLAPM_OK;
 }
 
@@ -1177,18 +1212,27 @@ int colapm_get_timing(colapm_ctx* c, double* ms, long long* launches) {
 // ---------------------------------------------------------------------------------------------
 // Autotuning: FFT engine and particle-kernel block size, timed on the context's own state.
 
-static std::mutex g_tune_mu;
-struct Tuned {
-    bool two_stage;
-    int fused, block;
-};
-static std::map<std::pair<int, int>, Tuned> g_tuned;   // (np, nm) -> choice
 
 int colapm_set_engine(colapm_ctx* c, int fused, int two_stage, int block) {
     if (!c || (block != 128 && block != 256 && block != 512) || fused < 0 || fused > 3) return COLAPM_E_ARG;
     c->fused = fused;
-    c->two_stage = two_stage != 0;
+    c->plan = two_stage ? COLAPM_PLAN_ALL : 0u;
     c->block = block;
+    return COLAPM_OK;
+}
+
+int colapm_set_plan(colapm_ctx* c, int plan) {
+    if (!c || plan < 0 || plan > (int)COLAPM_PLAN_ALL) return COLAPM_E_ARG;
+    c->plan = (unsigned)plan;
+    return COLAPM_OK;
+}
+
+int colapm_get_config(const colapm_ctx* c, int* cfg) {
+    if (!c || !cfg) return COLAPM_E_ARG;
+    cfg[0] = (int)c->plan;
+    cfg[1] = c->block;
+    cfg[2] = c->xy_ring ? c->fused : 0;
+    cfg[3] = c->sort_every;
     return COLAPM_OK;
 }
 
@@ -1206,7 +1250,8 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     CK(cudaMemcpyAsync(snap, c->pos, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(snap + 4 * c->np3, c->mom, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     const int step0 = c->step;
-    const bool fin0 = c->finalized, t0 = c->two_stage;
+    const bool fin0 = c->finalized;
+    const unsigned p0 = c->plan;
     const int f0 = c->fused;
     const int b0 = c->block;
     const bool timing0 = c->timing;
@@ -1215,45 +1260,69 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    bool best_ts = t0;
-    int best_f = f0;
-    int best_b = b0;
-    const int blocks[3] = {128, 256, 512};
     const int ksteps = c->prm.n_steps - 1 < step0 ? 0 : 1;
     int r = COLAPM_OK;
-    // engines: 0 fused x-y passes (where the mesh size has them), 1 two-stage, 2 Stockham
+    // One force computation + gather from the snapshot in configuration (plan, fused, block): the
+    // fastest of three repetitions after one warm-up, in ms (infinite on an error).
+    auto trial = [&](unsigned plan, int fused, int block) -> float {
+        c->plan = plan;
+        c->fused = fused;
+        c->block = block;
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 4 && r == COLAPM_OK; ++rep) {
+            if (cudaMemcpyAsync(c->pos, snap, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(c->mom, snap + 4 * c->np3, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                c->stream) != cudaSuccess) {
+                r = COLAPM_E_CUDA;
+                break;
+            }
+            c->step = ksteps ? step0 : 0;
+            cudaEventRecord(e0, c->stream);
+            r = compute_force(c);
+            if (r == COLAPM_OK && cudaGetLastError() == cudaSuccess) {
+                const int i = c->step < c->prm.n_steps ? c->step : c->prm.n_steps - 1;
+                if (launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, force_mesh(c), c->np3, c->nm, coef_for(c, i), 1,
+                                             c->stream, c->block) != cudaSuccess)
+                    r = COLAPM_E_CUDA;
+            }
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) r = COLAPM_E_CUDA;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best_ms) best_ms = ms;
+        }
+        return r == COLAPM_OK ? best_ms : 1e30f;
+    };
+    float best = 1e30f;
+    unsigned best_p = p0;
+    int best_f = f0;
+    int best_b = b0;
+    // 1. engines (fused x-y passes where the mesh size has them, all passes two-stage, all
+    //    Stockham) x particle-kernel block sizes
+    const int blocks[3] = {128, 256, 512};
     for (int eng = c->xy_ring ? 0 : 1; eng < 3 && r == COLAPM_OK; ++eng) {
         for (int bi = 0; bi < 3 && r == COLAPM_OK; ++bi) {
-            c->fused = eng == 0 ? 3 : 0;
-            c->two_stage = eng < 2;
-            c->block = blocks[bi];
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2 && r == COLAPM_OK; ++rep) {   // first repetition warms up
-                if (cudaMemcpyAsync(c->pos, snap, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
-                    cudaMemcpyAsync(c->mom, snap + 4 * c->np3, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice,
-                                    c->stream) != cudaSuccess) {
-                    r = COLAPM_E_CUDA;
-                    break;
-                }
-                c->step = ksteps ? step0 : 0;
-                cudaEventRecord(e0, c->stream);
-                r = compute_force(c);
-                if (r == COLAPM_OK && cudaGetLastError() == cudaSuccess) {
-                    const int i = c->step < c->prm.n_steps ? c->step : c->prm.n_steps - 1;
-                    if (launch_gather_kick_drift(c->pos, c->mom, c->psi1, c->psi2, force_mesh(c), c->np3, c->nm, coef_for(c, i), 1,
-                                                 c->stream, c->block) != cudaSuccess)
-                        r = COLAPM_E_CUDA;
-                }
-                cudaEventRecord(e1, c->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) r = COLAPM_E_CUDA;
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
-            if (r == COLAPM_OK && ms < best) {
+            const unsigned plan = eng < 2 ? COLAPM_PLAN_ALL : 0u;
+            const int fused = eng == 0 ? 3 : 0;
+            const float ms = trial(plan, fused, blocks[bi]);
+            if (ms < best) {
                 best = ms;
-                best_ts = c->two_stage;
-                best_f = c->fused;
-                best_b = c->block;
+                best_p = plan;
+                best_f = fused;
+                best_b = blocks[bi];
+            }
+        }
+    }
+    // 2. the radix plan per pass: starting from the best separate-pass engine, switch each pass
+    //    (forward x, y both ways, z, inverse x) to the other plan and keep what is faster
+    if (best_f == 0) {
+        const unsigned bits[4] = {COLAPM_PLAN_XF, COLAPM_PLAN_Y, COLAPM_PLAN_Z, COLAPM_PLAN_XI};
+        for (int k = 0; k < 4 && r == COLAPM_OK; ++k) {
+            const unsigned plan = best_p ^ bits[k];
+            const float ms = trial(plan, 0, best_b);
+            if (ms < best) {
+                best = ms;
+                best_p = plan;
             }
         }
     }
@@ -1266,20 +1335,20 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     c->finalized = fin0;
     c->timing = timing0;
     if (r != COLAPM_OK) {
-        c->two_stage = t0;
+        c->plan = p0;
         c->fused = f0;
         c->block = b0;
         return r;
     }
-    c->two_stage = best_ts;
+    c->plan = best_p;
     c->fused = best_f;
     c->block = best_b;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[{c->np, c->nm}] = Tuned{best_ts, best_f, best_b};
+        g_tuned[{c->np, c->nm}] = Tuned{best_p, best_f, best_b};
     }
     if (choice) {
-        choice[0] = best_ts ? 1 : 0;
+        choice[0] = best_p == COLAPM_PLAN_ALL ? 1 : 0;
         choice[1] = best_b;
         choice[2] = c->xy_ring ? best_f : 0;
     }
@@ -1305,6 +1374,11 @@ struct colapm_batch {
     int nbins = 0;
     double kmin = 0.0, kmax = 0.0;
     cudaGraphExec_t exec = nullptr;
+    bool lockstep = true;                   // step all mocks together with the multi-mock particle kernels
+    int max_steps = 0;                      // the largest n_steps of the batch
+    MockWork* work_h = nullptr;             // pinned [max_steps][n]: the multi-mock descriptors of each step
+    MockWork* work_d = nullptr;             // device copy
+    unsigned long long* queue_d = nullptr;  // work-ticket counters of the two multi-mock kernels (4 u64)
 };
 
 namespace {
@@ -1321,11 +1395,97 @@ void batch_free(colapm_batch* b) {
     if (b->seeds_h) cudaFreeHost(b->seeds_h);
     if (b->seeds_d) cudaFree(b->seeds_d);
     if (b->acc_h) cudaFreeHost(b->acc_h);
+    if (b->work_h) cudaFreeHost(b->work_h);
+    if (b->work_d) cudaFree(b->work_d);
+    if (b->queue_d) cudaFree(b->queue_d);
 }
 
-// Enqueue the whole batch on b->user (captured or eager): seeds, fork, per-mock ICs + steps +
-// P(k) on worker stream i mod K, copies of the accumulators to the pinned buffer, join.
+// Lockstep schedule: ICs of every mock (worker stream i mod K), then per step s one multi-mock
+// deposit of every mock still running, the mesh passes of each mock (worker streams), one
+// multi-mock gather-kick-drift, then the P(k) of every mock. The descriptors of step s are
+// written to the pinned buffer when the step is enqueued (with the particle arrays as they are
+// then: a reordering swaps them) and copied to the device in stream order.
+int batch_enqueue_lockstep(colapm_batch* b, int K) {
+    CK(cudaMemcpyAsync(b->seeds_d, b->seeds_h, b->n * sizeof(unsigned long long), cudaMemcpyHostToDevice, b->user));
+    auto fork = [&](int e) -> int {
+        CK(cudaEventRecord(b->ev[e], b->user));
+        for (int w = 0; w < K; ++w) CK(cudaStreamWaitEvent(b->ws[w], b->ev[e], 0));
+        return COLAPM_OK;
+    };
+    auto join = [&]() -> int {
+        for (int w = 0; w < K; ++w) {
+            CK(cudaEventRecord(b->ev[1 + w], b->ws[w]));
+            CK(cudaStreamWaitEvent(b->user, b->ev[1 + w], 0));
+        }
+        return COLAPM_OK;
+    };
+    int r = fork(0);
+    for (int i = 0; i < b->n && !r; ++i) {
+        colapm_ctx* c = b->ctx[i];
+        c->stream = b->ws[i % K];
+        r = colapm_make_ics(c);
+    }
+    if (!r) r = join();
+    for (int st = 0; st < b->max_steps && !r; ++st) {
+        MockWork* wh = b->work_h + (size_t)st * b->n;
+        int m = 0;
+        long long items = 0;
+        for (int i = 0; i < b->n && !r; ++i) {
+            colapm_ctx* c = b->ctx[i];
+            if (st >= c->prm.n_steps) continue;
+            c->stream = b->user;
+            if (c->sort_every > 0 && st > 0 && st % c->sort_every == 0) r = sort_particles(c);
+            if (!c->rho_clean && cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), b->user) != cudaSuccess)
+                r = COLAPM_E_CUDA;
+            c->rho_clean = false;
+            MockWork w{};
+            w.pos = c->pos;
+            w.mom = c->mom;
+            w.psi1 = c->psi1;
+            w.psi2 = c->psi2;
+            w.force = force_mesh(c);
+            w.rho = c->rho;
+            w.np3 = c->np3;
+            w.first = items;
+            w.nm = c->nm;
+            w.k = coef_for(c, st);
+            wh[m++] = w;
+            items += multi_items(c->np3);
+        }
+        if (r) break;
+        MockWork* wd = b->work_d + (size_t)st * b->n;
+        CK(cudaMemcpyAsync(wd, wh, m * sizeof(MockWork), cudaMemcpyHostToDevice, b->user));
+        CK(launch_multi_deposit(wd, m, items, b->queue_d, b->user));
+        r = fork(0);
+        for (int i = 0; i < b->n && !r; ++i) {
+            colapm_ctx* c = b->ctx[i];
+            if (st >= c->prm.n_steps) continue;
+            c->stream = b->ws[i % K];
+            r = force_from_density(c);
+        }
+        if (!r) r = join();
+        if (r) break;
+        CK(launch_multi_gather_kick_drift(wd, m, items, b->queue_d + 2, b->user));
+        for (int i = 0; i < b->n; ++i)
+            if (st < b->ctx[i]->prm.n_steps) ++b->ctx[i]->step;
+    }
+    if (!r) r = fork(0);
+    for (int i = 0; i < b->n && !r; ++i) {
+        colapm_ctx* c = b->ctx[i];
+        c->stream = b->ws[i % K];
+        r = power_enqueue(c, b->nbins);
+        if (!r && cudaMemcpyAsync(b->acc_h + (size_t)i * 3 * b->nbins, c->pw_acc, 3 * b->nbins * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            r = COLAPM_E_CUDA;
+    }
+    if (!r) r = join();
+    return r;
+}
+
+// Per-mock schedule: seeds, fork, per-mock ICs + steps + P(k) on worker stream i mod K, copies
+// of the accumulators to the pinned buffer, join.
 int batch_enqueue(colapm_batch* b, int K) {
+    if (b->lockstep) return batch_enqueue_lockstep(b, K);
     CK(cudaMemcpyAsync(b->seeds_d, b->seeds_h, b->n * sizeof(unsigned long long), cudaMemcpyHostToDevice, b->user));
     CK(cudaEventRecord(b->ev[0], b->user));
     for (int w = 0; w < K; ++w) CK(cudaStreamWaitEvent(b->ws[w], b->ev[0], 0));
@@ -1408,18 +1568,18 @@ int colapm_batch_create(int n, const colapm_params* ps, int nstreams, void* stre
     if (!r && (cudaMallocHost(&b->seeds_h, n * sizeof(unsigned long long)) != cudaSuccess ||
                cudaMalloc(&b->seeds_d, n * sizeof(unsigned long long)) != cudaSuccess))
         r = COLAPM_E_NOMEM;
+    for (int i = 0; i < n; ++i) b->max_steps = ps[i].n_steps > b->max_steps ? ps[i].n_steps : b->max_steps;
+    if (!r && b->max_steps > 0 &&
+        (cudaMallocHost(&b->work_h, (size_t)b->max_steps * n * sizeof(MockWork)) != cudaSuccess ||
+         cudaMalloc(&b->work_d, (size_t)b->max_steps * n * sizeof(MockWork)) != cudaSuccess ||
+         cudaMalloc(&b->queue_d, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+         cudaMemset(b->queue_d, 0, 4 * sizeof(unsigned long long)) != cudaSuccess))
+        r = COLAPM_E_NOMEM;
     for (int i = 0; i < n && !r; ++i) {
         r = colapm_create(&ps[i], b->ws[0], &b->ctx[i]);
         if (!r) {
             b->ctx[i]->seed_src = b->seeds_d + i;
             b->seeds_h[i] = ps[i].seed;
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto it = g_tuned.find({ps[i].np, ps[i].nm});
-            if (it != g_tuned.end()) {
-                b->ctx[i]->two_stage = it->second.two_stage;
-                b->ctx[i]->fused = it->second.fused;
-                b->ctx[i]->block = it->second.block;
-            }
         }
     }
     if (r) {
@@ -1448,6 +1608,30 @@ int colapm_batch_run(colapm_batch* b, const unsigned long long* seeds, int nbins
         b->nbins = nbins;
         b->kmin = kmin;
         b->kmax = kmax;
+        // Autotune every (np, nm) of the batch that has no tuned configuration in this process yet,
+        // on its first mock (after its ICs), and give the result to every mock of that size.
+        for (int i = 0; i < b->n; ++i) {
+            colapm_ctx* c = b->ctx[i];
+            bool known = false;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                known = g_tuned.count({c->np, c->nm}) != 0;
+            }
+            if (!known) {
+                c->stream = b->ws[0];
+                int r = colapm_make_ics(c);
+                if (!r) r = colapm_autotune(c, nullptr);
+                if (r) return r;
+            }
+            Tuned t{};
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                t = g_tuned.at({c->np, c->nm});
+            }
+            c->plan = t.plan;
+            c->fused = t.fused;
+            c->block = t.block;
+        }
         // One eager pass initialises every kernel's launch configuration before capture.
         int r = batch_enqueue(b, 1);
         if (r) return r;
@@ -1484,6 +1668,16 @@ int colapm_batch_run(colapm_batch* b, const unsigned long long* seeds, int nbins
 }
 
 int colapm_batch_streams(const colapm_batch* b) { return b ? b->nstreams : COLAPM_E_ARG; }
+
+int colapm_batch_set_lockstep(colapm_batch* b, int on) {
+    if (!b || on < 0 || on > 1) return COLAPM_E_ARG;
+    if (b->lockstep != (on == 1)) {
+        b->lockstep = on == 1;
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;   // the next run captures the other schedule
+    }
+    return COLAPM_OK;
+}
 
 void colapm_batch_destroy(colapm_batch* b) {
     if (!b) return;

@@ -113,7 +113,30 @@ struct LightconeStep {
     float a0, da, rl0, rl1;  // step start and width; lightcone radius at both ends, Mpc/h
 };
 
+// One mock of a multi-mock particle launch: its particle arrays, force meshes (gather), density
+// (deposit), sizes, step coefficients, and the index of its first work item (chunks of particles,
+// numbered mock after mock; multi_items gives a mock's count).
+struct MockWork {
+    float4* pos;
+    float* mom;
+    const float* psi1;
+    const float* psi2;
+    const float* force;
+    unsigned long long* rho;
+    size_t np3;
+    long long first;
+    int nm;
+    StepCoef k;
+};
+
 // --- launchers (pm_kernels.cu) --------------------------------------------------------------
+long long multi_items(size_t np3);
+// Deposit / gather-kick-drift of every mock in w[0..nmock) in one persistent launch; `queue` is two
+// zero-initialised u64 counters per kernel that the launch leaves at zero.
+cudaError_t launch_multi_deposit(const MockWork* w, int nmock, long long nitems, unsigned long long* queue,
+                                 cudaStream_t s);
+cudaError_t launch_multi_gather_kick_drift(const MockWork* w, int nmock, long long nitems, unsigned long long* queue,
+                                           cudaStream_t s);
 cudaError_t launch_deposit(const float4* pos, size_t np3, int nm, unsigned long long* rho, cudaStream_t s,
                            int block = 256);
 cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1, const float* psi2,

@@ -1,6 +1,6 @@
-// Two-stage register FFT for the large power-of-two mesh sizes (L = 256, 512, 1024).
+// Two-stage register FFT for the mesh lengths with a two-radix plan (L = 64 ... 1024).
 //
-// A line of length L = RA * RB (radices 16 or 32) is transformed in two Stockham stages. In
+// A line of length L = RA * RB (radices 8 to 32) is transformed in two Stockham stages. In
 // stage A (stride 1) task j < L/RA takes inputs j + r L/RA (r < RA) straight from global memory
 // (or from the caller), applies the RA-point DFT in registers and writes output r to position
 // j RA + r of a shared exchange buffer. In stage B (stride RA) task j < RA reads positions
@@ -25,17 +25,30 @@ namespace colapm {
 
 template <int L>
 struct F2;
+template <> struct F2<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct F2<96> { static constexpr int R1 = 8, R2 = 12; };
+template <> struct F2<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct F2<160> { static constexpr int R1 = 16, R2 = 10; };
+template <> struct F2<192> { static constexpr int R1 = 16, R2 = 12; };
 template <> struct F2<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct F2<320> { static constexpr int R1 = 16, R2 = 20; };
+template <> struct F2<384> { static constexpr int R1 = 16, R2 = 24; };
 template <> struct F2<512> { static constexpr int R1 = 16, R2 = 32; };
 template <> struct F2<1024> { static constexpr int R1 = 32, R2 = 32; };
 
+// Lengths with a two-stage plan. The mixed ones (96, 160, 192, 320, 384) take a composite second
+// radix (10, 12, 20, 24), itself split into coprime factors in registers (prime-factor algorithm).
 template <int L>
-struct F2Has { static constexpr bool value = L == 256 || L == 512 || L == 1024; };
+struct F2Has {
+    static constexpr bool value = L == 64 || L == 96 || L == 128 || L == 160 || L == 192 || L == 256 || L == 320 ||
+                                  L == 384 || L == 512 || L == 1024;
+};
 
 // Exchange buffer of LINES lines (8 by default) for a stage-A radix RA.
 template <int L, int RA, int LINES = 8>
 struct Xch {
-    static constexpr int PITCH = L + L / RA + 4;   // = 4 (mod 16) for the sizes above
+    static constexpr int BASE = L + L / RA;
+    static constexpr int PITCH = BASE + (((4 - BASE % 16) % 16) + 16) % 16;   // = 4 (mod 16)
     static constexpr int SIZE = LINES * PITCH;     // float2 elements
     __host__ __device__ __forceinline__ static int at(int c, int e) { return c * PITCH + e + e / RA; }
 };
@@ -631,7 +644,7 @@ __global__ void __launch_bounds__(X2<n>::T, 3) k2_fx_inv(float2* __restrict__ da
             for (int r = 0; r < RA; ++r) {
                 const int k = ja + r * (n / RA);
                 const float2 xk = row[k];
-                const float2 xm = row[(n - k) & (n - 1)];
+                const float2 xm = row[k == 0 ? 0 : n - k];
                 const float2 xc = k == 0 ? make_float2(0.0f, 0.0f) : cconj(xm);
                 const float2 E = cadd(xk, xc);
                 const float2 O = cmul(csub(xk, xc), cconj(tw[k]));

@@ -62,6 +62,23 @@ __host__ __device__ __forceinline__ float2 root(int k) {   // exp(S 2 pi i k / R
     return make_float2(c, S > 0 ? s : -s);
 }
 
+// Coprime split R = N1 N2 of the composite radices (N1 = 1: none), with the modular inverses
+// INV2 = N2^-1 mod N1 and INV1 = N1^-1 mod N2 of the output map.
+constexpr int inv_mod(int a, int m) {
+    for (int x = 1; x < m; ++x)
+        if ((a * x) % m == 1) return x;
+    return m == 1 ? 0 : -1;
+}
+template <int R>
+struct Pfa {
+    static constexpr int N1 = R == 6 ? 2 : R == 10 ? 2 : R == 12 ? 4 : R == 15 ? 3 : R == 20 ? 4 : R == 24 ? 8 :
+                              R == 40 ? 8 : R == 48 ? 16 : 1;
+    static constexpr int N2 = R / N1;
+    static constexpr int INV2 = N1 > 1 ? inv_mod(N2 % N1, N1) : 0;
+    static constexpr int INV1 = N1 > 1 ? inv_mod(N1 % N2, N2) : 0;
+    static_assert(N1 == 1 || (INV1 > 0 && INV2 > 0), "factors must be coprime");
+};
+
 // In-register R-point DFT, X_k = sum_m v_m exp(S 2 pi i m k / R).
 template <int R, int S>
 __host__ __device__ __forceinline__ void dft(float2* v) {
@@ -104,6 +121,29 @@ __host__ __device__ __forceinline__ void dft(float2* v) {
         v[4] = csub(a1, ib1);
         v[2] = cadd(a2, ib2);
         v[3] = csub(a2, ib2);
+    } else if constexpr (Pfa<R>::N1 > 1) {
+        // Good-Thomas prime-factor split R = N1 N2 (coprime): with the input map
+        // n = (N2 n1 + N1 n2) mod R and the Chinese-remainder output map k = k1 (mod N1),
+        // k = k2 (mod N2), exp(2 pi i n k / R) factors into exp(2 pi i n1 k1 / N1) exp(2 pi i n2 k2 / N2):
+        // an N2-point DFT of every row n1, then an N1-point DFT of every column k2, with no twiddles.
+        // All indices are compile-time constants, so the maps are register renaming only.
+        constexpr int N1 = Pfa<R>::N1, N2 = Pfa<R>::N2;
+        float2 a[N1][N2];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1)
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) a[n1][n2] = v[(N2 * n1 + N1 * n2) % R];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) dft<N2, S>(a[n1]);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            float2 col[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) col[n1] = a[n1][k2];
+            dft<N1, S>(col);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) v[(k1 * N2 * Pfa<R>::INV2 + k2 * N1 * Pfa<R>::INV1) % R] = col[k1];
+        }
     } else {
         static_assert(R == 8 || R == 16 || R == 32, "unsupported radix");
         float2 e[R / 2], o[R / 2];

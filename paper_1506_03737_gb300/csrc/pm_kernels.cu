@@ -9,6 +9,7 @@
 // (scale 2^45), accumulated with 64-bit integer atomics, so the mesh is independent of the
 // order in which particles arrive. The gather uses the same weights divided by 2^45.
 #include "colapm_internal.h"
+#include "launch_cache.h"
 
 namespace colapm {
 
@@ -41,11 +42,8 @@ __device__ __forceinline__ Cic cic_setup(float4 P, int nm) {
 // Two threads per particle, one per x corner (lane parity): the atomics of one warp instruction then
 // hit 16 particles x 2 neighbouring cells, which along the Lagrangian x rows are runs of consecutive
 // int64 cells (fully used 32-byte sectors), instead of every other cell of twice as many sectors.
-__global__ void k_deposit(const float4* __restrict__ pos, size_t np3, int nm, unsigned long long* __restrict__ rho) {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t p = t >> 1;
-    if (p >= np3) return;
-    const int dx = (int)(t & 1);
+__device__ __forceinline__ void deposit_corner(const float4* __restrict__ pos, size_t p, int dx, int nm,
+                                               unsigned long long* __restrict__ rho) {
     const Cic c = cic_setup(pos[p], nm);
     const unsigned long long wx = (unsigned long long)(dx ? c.fx : QONE - c.fx);
     const unsigned long long wy[2] = {(unsigned long long)(QONE - c.fy), (unsigned long long)c.fy};
@@ -58,6 +56,13 @@ __global__ void k_deposit(const float4* __restrict__ pos, size_t np3, int nm, un
             const unsigned long long w = wx * wy[dy] * wz[dz];
             if (w) atomicAdd(rho + ((size_t)zs[dz] * nm + ys[dy]) * nm + x, w);
         }
+}
+
+__global__ void k_deposit(const float4* __restrict__ pos, size_t np3, int nm, unsigned long long* __restrict__ rho) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t p = t >> 1;
+    if (p >= np3) return;
+    deposit_corner(pos, p, (int)(t & 1), nm, rho);
 }
 
 // Records the images of one particle that leave the past lightcone during the drift (§6): the image
@@ -110,11 +115,10 @@ __device__ __forceinline__ void record_lightcone(const LightconeStep& lc, const 
 }
 
 template <bool LC>
-__global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict__ mom, const float* __restrict__ psi1,
-                                    const float* __restrict__ psi2, const float* __restrict__ force, size_t np3, int nm,
-                                    StepCoef k, int drift, LightconeStep lc) {
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np3) return;
+__device__ __forceinline__ void gather_kick_drift(float4* __restrict__ pos, float* __restrict__ mom,
+                                                  const float* __restrict__ psi1, const float* __restrict__ psi2,
+                                                  const float* __restrict__ force, size_t np3, int nm, const StepCoef& k,
+                                                  int drift, const LightconeStep& lc, size_t p) {
     // every load of the particle's own data is issued before the force loads that depend on its
     // position, so the two sets are in flight together (streaming: each is used once per step)
     const float4 P = __ldcs(pos + p);
@@ -175,6 +179,93 @@ __global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict_
     }
     const unsigned lin = (unsigned)cell[0] + (unsigned)nm * ((unsigned)cell[1] + (unsigned)nm * (unsigned)cell[2]);
     __stcs(pos + p, make_float4(o[0], o[1], o[2], __uint_as_float(lin)));
+}
+
+template <bool LC>
+__global__ void k_gather_kick_drift(float4* __restrict__ pos, float* __restrict__ mom, const float* __restrict__ psi1,
+                                    const float* __restrict__ psi2, const float* __restrict__ force, size_t np3, int nm,
+                                    StepCoef k, int drift, LightconeStep lc) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np3) return;
+    gather_kick_drift<LC>(pos, mom, psi1, psi2, force, np3, nm, k, drift, lc, p);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Multi-mock particle kernels: one persistent launch for the particles of many mocks (any mix of
+// sizes). The work items are chunks of MW_ITEM particles, numbered mock after mock (w[m].first is
+// mock m's first item). Each CTA takes the next item from a ticket counter, finds its mock by
+// binary search over the `first` column, and runs the single-mock code on that chunk, until the
+// tickets run out. The last CTA to leave resets the counter for the next launch (queue[1] counts
+// the CTAs that left), so a captured graph can replay the launch without a memset. There is no
+// wait of any kind: a CTA only ever takes tickets.
+constexpr int MW_ITEM = 256;
+constexpr int MW_T = 256;
+
+__device__ __forceinline__ bool next_item(const MockWork* __restrict__ w, int nmock, long long nitems,
+                                          unsigned long long* queue, long long& item, int& mock) {
+    __shared__ long long s_item;
+    __shared__ int s_mock;
+    __syncthreads();   // the previous item's values are no longer read
+    if (threadIdx.x == 0) {
+        const long long it = (long long)atomicAdd(queue, 1ull);
+        int lo = 0, hi = nmock - 1;
+        while (lo < hi) {   // last mock whose first item is <= it
+            const int mid = (lo + hi + 1) >> 1;
+            if (w[mid].first <= it) lo = mid; else hi = mid - 1;
+        }
+        s_item = it;
+        s_mock = lo;
+    }
+    __syncthreads();
+    item = s_item;
+    mock = s_mock;
+    return item < nitems;
+}
+
+__device__ __forceinline__ void leave_queue(unsigned long long* queue) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+            queue[0] = 0ull;
+            queue[1] = 0ull;
+            __threadfence();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MW_T) k_multi_deposit(const MockWork* __restrict__ w, int nmock, long long nitems,
+                                                        unsigned long long* queue) {
+    long long item;
+    int m;
+    while (next_item(w, nmock, nitems, queue, item, m)) {
+        const MockWork& mw = w[m];
+        const size_t base = (size_t)(item - mw.first) * MW_ITEM;
+#pragma unroll
+        for (int h = 0; h < 2 * MW_ITEM / MW_T; ++h) {   // two threads per particle, one per x corner
+            const int slot = h * MW_T + threadIdx.x;
+            const size_t p = base + (slot >> 1);
+            if (p < mw.np3) deposit_corner(mw.pos, p, slot & 1, mw.nm, mw.rho);
+        }
+    }
+    leave_queue(queue);
+}
+
+__global__ void __launch_bounds__(MW_T) k_multi_gather_kick_drift(const MockWork* __restrict__ w, int nmock,
+                                                                  long long nitems, unsigned long long* queue) {
+    long long item;
+    int m;
+    while (next_item(w, nmock, nitems, queue, item, m)) {
+        const MockWork& mw = w[m];
+        const size_t base = (size_t)(item - mw.first) * MW_ITEM;
+#pragma unroll
+        for (int h = 0; h < MW_ITEM / MW_T; ++h) {
+            const size_t p = base + h * MW_T + threadIdx.x;
+            if (p < mw.np3)
+                gather_kick_drift<false>(mw.pos, mw.mom, mw.psi1, mw.psi2, mw.force, mw.np3, mw.nm, mw.k, 1,
+                                         LightconeStep{}, p);
+        }
+    }
+    leave_queue(queue);
 }
 
 // Site i of the Lagrangian lattice sits at mesh coordinate i nm / np + 1/2 (spacing L / np, offset by
@@ -420,6 +511,30 @@ cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1,
     else
         k_gather_kick_drift<false><<<blocks(np3, block), block, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift,
                                                                         LightconeStep{});
+    return cudaGetLastError();
+}
+
+long long multi_items(size_t np3) { return (long long)((np3 + MW_ITEM - 1) / MW_ITEM); }
+
+cudaError_t launch_multi_deposit(const MockWork* w, int nmock, long long nitems, unsigned long long* queue,
+                                 cudaStream_t s) {
+    static GridCache cache;
+    int grid = 0;
+    cudaError_t e = cached_grid(cache, k_multi_deposit, MW_T, 0, &grid);
+    if (e != cudaSuccess) return e;
+    if (nitems < 1 || nmock < 1) return cudaSuccess;
+    k_multi_deposit<<<nitems < grid ? (int)nitems : grid, MW_T, 0, s>>>(w, nmock, nitems, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multi_gather_kick_drift(const MockWork* w, int nmock, long long nitems, unsigned long long* queue,
+                                           cudaStream_t s) {
+    static GridCache cache;
+    int grid = 0;
+    cudaError_t e = cached_grid(cache, k_multi_gather_kick_drift, MW_T, 0, &grid);
+    if (e != cudaSuccess) return e;
+    if (nitems < 1 || nmock < 1) return cudaSuccess;
+    k_multi_gather_kick_drift<<<nitems < grid ? (int)nitems : grid, MW_T, 0, s>>>(w, nmock, nitems, queue);
     return cudaGetLastError();
 }
 

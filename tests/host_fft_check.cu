@@ -2,7 +2,9 @@
 // their two stages with a block barrier, so running stage A for every task, then stage B for every
 // task, reproduces a tile exactly. The checks use the header's own DFT, twiddle and exchange-buffer
 // code:
-//  - forward (radices R1, R2) and inverse transforms of 8 lines against an FP64 DFT;
+//  - every composite register radix (prime-factor split) against an FP64 DFT;
+//  - forward (radices R1, R2) and inverse transforms of 8 lines against an FP64 DFT, at every
+//    length with a two-stage plan (64 ... 1024, including the mixed 96, 160, 192, 320, 384);
 //  - the z-pass chain: the forward stage-B outputs of task j, fed unchanged to stage A of the
 //    inverse with the radices swapped, give back L times the input.
 // Exit status 0 when every check passes.
@@ -104,9 +106,48 @@ static int check() {
     return rel < 2e-6 ? 0 : 1;
 }
 
+// One R-point register DFT (composite R: the prime-factor split) against an FP64 DFT, both signs.
+template <int R>
+static int check_radix() {
+    unsigned s = 777u + R;
+    auto rnd = [&s] { s = s * 1664525u + 1013904223u; return (float)((s >> 8) * (1.0 / 16777216.0) - 0.5); };
+    float2 x[R];
+    for (auto& e : x) e = make_float2(rnd(), rnd());
+    double worst = 0.0;
+    for (int dir = -1; dir <= 1; dir += 2) {
+        float2 v[R];
+        for (int m = 0; m < R; ++m) v[m] = x[m];
+        if (dir < 0) colapm::dft<R, -1>(v);
+        else colapm::dft<R, +1>(v);
+        double err = 0.0, ref = 0.0;
+        for (int k = 0; k < R; ++k) {
+            double re = 0.0, im = 0.0;
+            for (int m = 0; m < R; ++m) {
+                const double a = dir * 2.0 * M_PI * (double)(m * k % R) / R;
+                re += x[m].x * std::cos(a) - x[m].y * std::sin(a);
+                im += x[m].x * std::sin(a) + x[m].y * std::cos(a);
+            }
+            err += (v[k].x - re) * (v[k].x - re) + (v[k].y - im) * (v[k].y - im);
+            ref += re * re + im * im;
+        }
+        worst = std::fmax(worst, std::sqrt(err / ref));
+    }
+    std::printf("radix %d: rms rel error %.2e\n", R, worst);
+    return worst < 1e-6 ? 0 : 1;
+}
+
 int main() {
     int bad = 0;
+    bad |= check_radix<6>() | check_radix<10>() | check_radix<12>() | check_radix<15>() | check_radix<20>() |
+           check_radix<24>() | check_radix<40>() | check_radix<48>();
+    bad |= check<64>();
+    bad |= check<96>();
+    bad |= check<128>();
+    bad |= check<160>();
+    bad |= check<192>();
     bad |= check<256>();
+    bad |= check<320>();
+    bad |= check<384>();
     bad |= check<512>();
     bad |= check<1024>();
     return bad;

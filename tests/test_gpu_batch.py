@@ -96,6 +96,70 @@ def test_autotune_preserves_state_and_results(C):
         C.colapm_destroy(b)
 
 
+def test_lockstep_and_per_mock_schedules_agree_bit_for_bit(C):
+    """The lockstep schedule (multi-mock persistent deposit and gather over work items of every
+    mock, uneven sizes and step counts) against each mock run on its own, in one batch: identical
+    P(k), replay after replay (the ticket counters reset themselves)."""
+    params = [C.default_params(np=a, nm=b, box=L, seed=700 + i, n_steps=4 + (i % 3)) for i, (a, b, L) in enumerate(MOCKS)]
+    b = C.colapm_batch_create(params, nstreams=2)
+    try:
+        nbins = 16
+        seeds = [40 + i for i in range(len(params))]
+        C.colapm_batch_set_lockstep(b, True)
+        k1, p1, n1 = C.colapm_batch_run(b, len(params), nbins, seeds=seeds)
+        k1b, p1b, _ = C.colapm_batch_run(b, len(params), nbins, seeds=seeds)
+        C.colapm_batch_set_lockstep(b, False)
+        k2, p2, n2 = C.colapm_batch_run(b, len(params), nbins, seeds=seeds)
+        assert np.array_equal(n1, n2)
+        assert np.array_equal(p1, p2, equal_nan=True) and np.array_equal(k1, k2, equal_nan=True)
+        assert np.array_equal(p1, p1b, equal_nan=True)
+        assert C.LIB.colapm_batch_set_lockstep(b, 2) == C.LIB.colapm_batch_set_lockstep(None, 1) != 0
+    finally:
+        C.colapm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("np_,nm", [(96, 192), (160, 320), (256, 512)])
+def test_every_plan_mask_gives_the_same_force(C, np_, nm):
+    """Each pass on either radix plan (16 masks; at 512^3 only the all-two-stage mask keeps the
+    blocked layout): the force meshes agree to FP32 rounding, and the autotuner's choice is one of
+    them and is reported whole by colapm_get_config."""
+    import torch
+    ctx = C.colapm_create(C.default_params(np=np_, nm=nm, box=300.0, seed=3))
+    try:
+        C.colapm_make_ics(ctx)
+        C.colapm_step(ctx, 4)
+        out = {}
+        for plan in range(16):
+            C.colapm_set_plan(ctx, plan)
+            f = torch.empty(3 * nm ** 3, dtype=torch.float32, device="cuda")
+            C.colapm_get_force(ctx, f)
+            out[plan] = f
+        ref = out[C.PLAN_ALL].double()
+        scale = torch.sqrt(torch.mean(ref ** 2)).item()
+        for plan, f in out.items():
+            diff = f.double() - ref
+            assert torch.sqrt(torch.mean(diff ** 2)).item() < 1e-5 * scale, plan
+        if nm < 512:   # (tuning is remembered per size for the rest of the process)
+            C.colapm_autotune(ctx)
+            cfg = C.colapm_get_config(ctx)
+            assert 0 <= cfg["plan"] <= C.PLAN_ALL and cfg["block"] in (128, 256, 512)
+            assert C.colapm_steps_done(ctx) == 4
+    finally:
+        C.colapm_destroy(ctx)
+
+
+def test_plan_arguments_are_checked(C):
+    ctx = C.colapm_create(C.default_params(np=16, nm=32, box=100.0))
+    try:
+        for bad in (-1, 16):
+            with pytest.raises(C.ColapmError):
+                C.colapm_set_plan(ctx, bad)
+        C.colapm_set_plan(ctx, C.PLAN_Y | C.PLAN_Z)
+        assert C.colapm_get_config(ctx)["plan"] == C.PLAN_Y | C.PLAN_Z
+    finally:
+        C.colapm_destroy(ctx)
+
+
 def test_uneven_batch_mocks_match_oracle_at_full_size(C):
     """Mocks r = 0..7 of the 64-mock uneven batch (N_p = 64 + 32 (r mod 5), N_m = 2 N_p,
     L = 128 + 96 (r mod 5) Mpc/h, seed 1000 + r, 10 steps): every mock equals a single context,

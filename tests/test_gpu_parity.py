@@ -190,6 +190,33 @@ def test_force_mesh_matches_oracle(C, np_, nm, deconv):
         s.close()
 
 
+@pytest.mark.parametrize("np_,nm", [(32, 64), (32, 96), (64, 128), (32, 160), (96, 192)])
+@pytest.mark.parametrize("two_stage", [1, 0])
+def test_force_engines_match_oracle(C, np_, nm, two_stage):
+    """Both FFT engines against the oracle at the power-of-two and mixed-radix sizes of the batch:
+    the two-stage register plans (second radix 8, 10, 12 by the prime-factor split) and the
+    multi-stage Stockham plans, each in every pass, with the whole step chain behind it."""
+    s = Sim(C, np=np_, nm=nm, box=250.0)
+    try:
+        C.colapm_set_engine(s.ctx, 0, two_stage, 256)
+        C.colapm_make_ics(s.ctx)
+        cell, off, _ = workloads.clustered_state(np_, nm, 7)
+        C.colapm_set_state(s.ctx, cell, off, None)
+        gpu = s.force()
+        rho = opm.cic_deposit(mesh_coords(cell, off), nm)
+        ref = opm.force_mesh(opm.density_contrast(rho, np_, nm), s.box, 1) * (nm / s.box)
+        for j in range(3):
+            assert rel_rms(gpu[j], ref[j]) < 1e-4, j
+        k, p, cnt = C.colapm_power(s.ctx, 20)
+        kr, pr, nr = opower.power_from_positions(mesh_coords(cell, off) * (s.box / nm), s.box, np_, nm, 20,
+                                                 fft="numpy")
+        assert np.array_equal(cnt, nr)
+        ok = nr > 0
+        assert np.max(np.abs(p[ok] / pr[ok] - 1)) < 1e-4
+    finally:
+        s.close()
+
+
 # --- one step from a shared state ----------------------------------------------------------
 
 @pytest.mark.parametrize("cola_on,stepping,spacing", [(1, 0, 0), (0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)])
