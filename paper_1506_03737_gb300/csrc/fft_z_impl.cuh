@@ -5,27 +5,45 @@
 
 #include "fft2.cuh"
 #include "fft_kernels.cuh"
+#include "fft_pair.cuh"
+
 
 namespace colapm {
 
 template <int N, int MODE, bool BLK>
 static cudaError_t fz2(float2* in, ZOut out, const float2* tw, const float* sinc2, int deconv, float gnorm, PowerArgs pw,
                        cudaStream_t s) {
-    // Blocked layout: 4-column tiles (32-byte rows whose 512-byte runs the neighbouring tiles
-    // complete), which with the prefetch buffer measured 2% faster than 8-column ones (34% for the
-    // power spectrum), and with direct loads fit three CTAs per SM. Standard layout: 8 columns
-    // (4-column rows there are 32 bytes 4 MB apart).
-    constexpr int CZ = BLK ? 4 : 8;
-    constexpr bool DIRECT = BLK;   // blocked layout: loads straight into registers, three CTAs per SM
-    using Z = Z2<N, MODE, CZ, DIRECT>;
-    const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
-    static GridCache cache;
-    int grid2 = 0;
-    cudaError_t e = cached_grid(cache, k2_fz<N, MODE, CZ, BLK, DIRECT>, Z::T, smem, &grid2);
-    if (e != cudaSuccess) return e;
-    const int total = (N / 2 / CZ) * N;
-    k2_fz<N, MODE, CZ, BLK, DIRECT><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
-    return cudaGetLastError();
+    if constexpr (N == 1024 && MODE == Z_FORCE && BLK) {
+        // 1024-point force lines: each radix-32 task on a pair of lanes (16 values per thread),
+        // two CTAs of 256 threads per SM (measured at 1024^3: 4.93 ms against 5.50 for the
+        // one-thread-per-task kernel at three CTAs of 128 threads, 6.1-6.4 ms with the pair kernel
+        // held to 80 registers for three CTAs, 5.32 ms with the next tile's inputs loaded into
+        // registers during the inverse transforms)
+        constexpr int MINB = 2;
+        static GridCache cache;
+        int grid = 0;
+        cudaError_t e = cached_grid(cache, k2_fz_pair<MINB>, PZ_T, PairZ<MINB>::SMEM, &grid);
+        if (e != cudaSuccess) return e;
+        const int total = (N / 2 / 4) * N;
+        k2_fz_pair<MINB><<<grid < total ? grid : total, PZ_T, PairZ<MINB>::SMEM, s>>>(in, out, tw, sinc2, deconv, gnorm);
+        return cudaGetLastError();
+    } else {
+        // Blocked layout: 4-column tiles (32-byte rows whose 512-byte runs the neighbouring tiles
+        // complete), which with the prefetch buffer measured 2% faster than 8-column ones (34% for the
+        // power spectrum), and with direct loads fit three CTAs per SM. Standard layout: 8 columns
+        // (4-column rows there are 32 bytes 4 MB apart).
+        constexpr int CZ = BLK ? 4 : 8;
+        constexpr bool DIRECT = BLK;   // blocked layout: loads straight into registers, three CTAs per SM
+        using Z = Z2<N, MODE, CZ, DIRECT>;
+        const size_t smem = Z::SMEM + (MODE == Z_POWER ? (size_t)pw.nbins * 24 + (size_t)(pw.nbins + 1) * 4 : 0);
+        static GridCache cache;
+        int grid2 = 0;
+        cudaError_t e = cached_grid(cache, k2_fz<N, MODE, CZ, BLK, DIRECT>, Z::T, smem, &grid2);
+        if (e != cudaSuccess) return e;
+        const int total = (N / 2 / CZ) * N;
+        k2_fz<N, MODE, CZ, BLK, DIRECT><<<grid2 < total ? grid2 : total, Z::T, smem, s>>>(in, out, tw, sinc2, deconv, gnorm, pw);
+        return cudaGetLastError();
+    }
 }
 
 template <int N, int MODE>

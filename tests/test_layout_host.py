@@ -33,3 +33,10 @@ def test_register_fft_against_fp64_dft(tmp_path):
     out = build_and_run("host_fft_check.cu", tmp_path / "fft_check")
     assert sum(line.startswith("radix ") for line in out.splitlines()) == 8
     assert out.count("rms rel error") == 8 + 3 * 10
+
+
+def test_paired_lane_transforms_against_fp64_dft(tmp_path):
+    """The 1024-point force z pass with each radix-32 task split over two lanes: both exchange forms
+    (decimation in time and in frequency) and the whole tile chain, with the header's own code."""
+    out = build_and_run("host_pair_check.cu", tmp_path / "pair_check")
+    assert out.count("rms rel error") == 6
