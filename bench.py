@@ -49,12 +49,16 @@ STEP_PHASES = ("sort", "deposit", "fft_fwd", "poisson", "fft_inv", "fft_inv_x", 
 # 1073.9 + 1546.3, gather 2494.7 + 454.1, deposit 1243.8 + 792.8.
 DRAM_512 = {"poisson": 1556.0e6, "fft_inv_x": 3172.3e6, "fft_inv": 2620.2e6, "gather": 2948.8e6,
             "deposit": 2036.6e6}
+# Phases that run another kernel at 1024^3 than the one measured at 512^3 (the force z pass there
+# is the paired-lane kernel): their DRAM bytes per launch measured at 1024^3 (4515.6 + 8688.3 MB).
+DRAM_1024 = {"poisson": 13203.9e6}
 
 
 def roofline(phase_ms, phase_n, np_, nm, hbm):
     """Roofline object of the dominant kernel: the single-kernel phase with the largest total time.
     achieved = its algorithmic bytes per call / its mean call time; traffic = the ncu DRAM bytes
-    per call measured at 512^3, scaled by the cell count (None off the N_m = 2 N_p family)."""
+    per call measured at 512^3, scaled by the cell count (None off the N_m = 2 N_p family), or
+    measured at 1024^3 for a kernel that only runs there."""
     dom = max(DRAM_512, key=lambda k: phase_ms[k])
     units = {"cell": nm ** 3, "particle": np_ ** 3}
     unit, b = ALG_PHASE[dom]
@@ -63,7 +67,10 @@ def roofline(phase_ms, phase_n, np_, nm, hbm):
         nbytes += EXTRA[dom][1] * units[EXTRA[dom][0]]
     per_call_ms = phase_ms[dom] / max(int(phase_n[dom]), 1)
     achieved = nbytes / (per_call_ms / 1e3) / 1e9
-    traffic = DRAM_512[dom] / 512 ** 3 * nm ** 3 if nm == 2 * np_ else None
+    if nm == 1024 and dom in DRAM_1024:
+        traffic = DRAM_1024[dom]
+    else:
+        traffic = DRAM_512[dom] / 512 ** 3 * nm ** 3 if nm == 2 * np_ else None
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "alg_bytes": nbytes}
 
@@ -83,6 +90,8 @@ def parse():
     ap.add_argument("--no-study", action="store_true")
     ap.add_argument("--sort", type=int, default=None,
                     help="reorder the particles by cell every K steps (profiling aid; the default is the library's)")
+    ap.add_argument("--deposit-tiles", type=int, default=None,
+                    help="deposit tiles of 64 x T x T cells, T in 0, 2, 4, 8 (profiling aid; the default is the library's)")
     ap.add_argument("--engine", default="default", choices=["default", "fused", "two_stage", "stockham"],
                     help="FFT engine of the timed context (profiling aid; the default is the library's)")
     return ap.parse_args()
@@ -439,6 +448,8 @@ def main():
         C.colapm_set_engine(ctx, fused, two, 256)
     if args.sort is not None:
         C.colapm_set_sort(ctx, args.sort)
+    if args.deposit_tiles is not None:
+        C.colapm_set_deposit_tiles(ctx, args.deposit_tiles)
     nbins = 100
     kd = torch.empty(nbins, dtype=torch.float64, device="cuda")
     pd = torch.empty(nbins, dtype=torch.float64, device="cuda")

@@ -296,9 +296,13 @@ long long colapm_kernel_launches(const colapm_ctx* ctx);
  *      pass two-stage, or every pass Stockham -- times the block size of the particle kernels
  *      (128, 256, 512);
  *   2. then, unless the fused passes won, the radix plan of each pass (COLAPM_PLAN_* bits) in
- *      turn: a pass switched to the other plan is kept if the step gets faster.
- * Each candidate is one force computation and gather from the same state (fastest of three after
- * a warm-up). The particle state and step counter are restored. Requires initial conditions
+ *      turn: a pass switched to the other plan is kept if the step gets faster;
+ *   3. where the context reorders its particles (colapm_set_sort), the deposit tile shape
+ *      (colapm_set_deposit_tiles: 0, 2, 4, 8): the particles are sorted with each shape's key and
+ *      the deposit alone is timed.
+ * Each candidate of 1 and 2 is one force computation and gather from the same state (fastest of
+ * three after a warm-up); the particle state and step counter are then restored, and step 3 leaves
+ * the particles in the order of the shape kept (no result depends on the order). Requires initial conditions
  * (COLAPM_E_STATE). Synchronises. `choice` (may be NULL, else 3 ints) receives {1 if every pass is
  * two-stage else 0, block, fused x-y passes (0 or 3)}; colapm_get_config gives the whole choice. */
 int colapm_autotune(colapm_ctx* ctx, int* choice);
@@ -315,8 +319,8 @@ int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
  * uses the plain layout there. COLAPM_E_ARG outside 0 ... COLAPM_PLAN_ALL. */
 int colapm_set_plan(colapm_ctx* ctx, int plan);
 
-/* The context's configuration: cfg (4 ints) = {plan mask, particle-kernel block size, fused x-y
- * passes (0 where N_m has none), sort cadence (colapm_set_sort)}. */
+/* The context's configuration: cfg (5 ints) = {plan mask, particle-kernel block size, fused x-y
+ * passes (0 where N_m has none), sort cadence (colapm_set_sort), deposit tile T (0: none)}. */
 int colapm_get_config(const colapm_ctx* ctx, int* cfg);
 
 /* Reorder the particle arrays by mesh cell before every `every`-th step (0: never). The default is
@@ -328,6 +332,17 @@ int colapm_get_config(const colapm_ctx* ctx, int* cfg);
  * sum), and calls that take or return particle arrays still use particle-id order.
  * COLAPM_E_ARG for every < 0. */
 int colapm_set_sort(colapm_ctx* ctx, int every);
+
+/* Deposit tiles of 64 x T x T cells (T = 2, 4 or 8, N_m a multiple of T; 0: none, the default).
+ * The reordering then sorts the particles tile by tile (inside a tile by runs of 64 cells along x),
+ * and while they are in that order the deposit gives each tile's particles to one CTA, which adds
+ * their corners inside the tile and its +1 halo into shared memory with 64-bit shared atomics and
+ * then adds the (T + 1)^2 x 65 region to the mesh, one atomic per non-zero cell; corners of
+ * particles that moved out of that region since the sort go straight to the mesh. The mesh is the
+ * same integer sum bit for bit (the analogue of the paper's per-rank density slab, §4: each tile is
+ * summed where its particles are, then added into the global mesh). Takes effect at the next
+ * reordering. COLAPM_E_ARG for other T. */
+int colapm_set_deposit_tiles(colapm_ctx* ctx, int t);
 
 /* ---- batched mocks (many independent realisations of uneven sizes) ----------------------- */
 typedef struct colapm_batch colapm_batch;   /* opaque; owns its contexts and graph */

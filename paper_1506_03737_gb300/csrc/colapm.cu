@@ -37,6 +37,8 @@ struct colapm_ctx {
     unsigned* sort_cnt = nullptr;        // bucket counters / cursors of the cell sort
     unsigned* sort_tile = nullptr;       // their tile sums
     int sort_every = 0;                  // reorder by cell before every k-th step (0: never)
+    int dep_tshift = 0;                  // sort key and deposit: tiles of 64 x 2^t x 2^t cells (0: rows, plain deposit)
+    int sorted_tshift = -1;              // tile shift of the order the particles are in (-1: id order)
     double fnl = 0.0;                    // local primordial non-Gaussianity of the next ICs
     float* fnl_tab = nullptr;            // per |n|^2 of the IC grid: 1 / (M N^3), then M (colapm_set_fnl)
     double* fnl_sum = nullptr;           // FP64 sum of phi^2
@@ -193,10 +195,18 @@ DepositSrc own_particles(const colapm_ctx* c) {
 }
 
 // Fixed-point CIC deposit into c's mesh of the given particles (default: c's own).
+// Whether the own particles are ordered by the tiles of the tiled deposit (the last sort used the
+// context's tile shape and nothing has restored id order since).
+bool tiles_ready(const colapm_ctx* c) { return c->dep_tshift > 0 && !c->id_order && c->sorted_tshift == c->dep_tshift; }
+
 int deposit(colapm_ctx* c, const DepositSrc* src = nullptr) {
     Phase ph(c, COLAPM_PHASE_DEPOSIT);
     if (!c->rho_clean) CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
     c->rho_clean = false;
+    if (!src && tiles_ready(c)) {
+        CKL(launch_deposit_tiles(c->pos, c->nm, c->dep_tshift, c->sort_cnt, c->rho, c->stream));
+        return COLAPM_OK;
+    }
     const DepositSrc d = src ? *src : own_particles(c);
     for (int i = 0; i < 2; ++i)
         if (d.pos[i]) CKL(launch_deposit(d.pos[i], d.n[i], c->nm, c->rho, c->stream, c->block));
@@ -235,9 +245,10 @@ void swap_particle_arrays(colapm_ctx* c) {
 // Reorder the particle arrays by mesh cell (counting sort into the second set, then swap).
 int sort_particles(colapm_ctx* c) {
     Phase ph(c, COLAPM_PHASE_SORT);
-    CKL(launch_sort(sort_buffers(c), c->np3, c->nm, c->stream));
+    CKL(launch_sort(sort_buffers(c), c->np3, c->nm, c->dep_tshift, c->stream));
     swap_particle_arrays(c);
     c->id_order = false;
+    c->sorted_tshift = c->dep_tshift;
     return COLAPM_OK;
 }
 
@@ -462,7 +473,7 @@ const char* colapm_strerror(int code) {
 static std::mutex g_tune_mu;
 struct Tuned {
     unsigned plan;
-    int fused, block;
+    int fused, block, dep_tshift;
 };
 static std::map<std::pair<int, int>, Tuned> g_tuned;   // (np, nm) -> choice
 
@@ -544,6 +555,7 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
             c->plan = it->second.plan;
             c->fused = it->second.fused;
             c->block = it->second.block;
+            c->dep_tshift = it->second.dep_tshift;
         }
     }
     *out = c;
@@ -1233,6 +1245,16 @@ int colapm_get_config(const colapm_ctx* c, int* cfg) {
     cfg[1] = c->block;
     cfg[2] = c->xy_ring ? c->fused : 0;
     cfg[3] = c->sort_every;
+    cfg[4] = c->dep_tshift > 0 ? 1 << c->dep_tshift : 0;
+    return COLAPM_OK;
+}
+
+int colapm_set_deposit_tiles(colapm_ctx* c, int t) {
+    if (!c) return COLAPM_E_ARG;
+    int ts = 0;
+    while (ts < 3 && (1 << ts) < t) ++ts;
+    if (t != 0 && (t != (1 << ts) || ts < 1 || !sort_tshift_ok(c->nm, ts))) return COLAPM_E_ARG;
+    c->dep_tshift = t == 0 ? 0 : ts;
     return COLAPM_OK;
 }
 
@@ -1329,12 +1351,12 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     cudaMemcpyAsync(c->pos, snap, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
     cudaMemcpyAsync(c->mom, snap + 4 * c->np3, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
     cudaStreamSynchronize(c->stream);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->step = step0;
     c->finalized = fin0;
     c->timing = timing0;
     if (r != COLAPM_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
         c->plan = p0;
         c->fused = f0;
         c->block = b0;
@@ -1343,9 +1365,43 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     c->plan = best_p;
     c->fused = best_f;
     c->block = best_b;
+    // 3. the deposit tile shape, where the context reorders its particles: for each shape the
+    //    particles are sorted with its key (the order changes no result) and the deposit is timed
+    //    alone; the particles are left in the order of the shape kept
+    int best_t = c->dep_tshift;
+    if (c->sort_every > 0) {
+        float best_dep = 1e30f;
+        for (int ts = 0; ts <= 3 && r == COLAPM_OK; ++ts) {
+            if (ts > 0 && !sort_tshift_ok(c->nm, ts)) continue;
+            c->dep_tshift = ts;
+            r = sort_particles(c);
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 4 && r == COLAPM_OK; ++rep) {
+                cudaEventRecord(e0, c->stream);
+                r = deposit(c);
+                cudaEventRecord(e1, c->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) r = COLAPM_E_CUDA;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < ms_best) ms_best = ms;
+            }
+            if (ms_best < best_dep) {
+                best_dep = ms_best;
+                best_t = ts;
+            }
+        }
+        if (r == COLAPM_OK && c->dep_tshift != best_t) {
+            c->dep_tshift = best_t;
+            r = sort_particles(c);
+        }
+        if (r == COLAPM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) r = COLAPM_E_CUDA;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != COLAPM_OK) return r;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[{c->np, c->nm}] = Tuned{best_p, best_f, best_b};
+        g_tuned[{c->np, c->nm}] = Tuned{best_p, best_f, best_b, best_t};
     }
     if (choice) {
         choice[0] = best_p == COLAPM_PLAN_ALL ? 1 : 0;

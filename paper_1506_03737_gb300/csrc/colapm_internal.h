@@ -183,7 +183,15 @@ int sort_xshift(int nm);
 size_t sort_buckets(int nm);
 size_t sort_tiles(int nm);
 // Counting sort of the particles by bucket (z, y, x >> sort_xshift) of their cell into the _o arrays.
-cudaError_t launch_sort(SortBuffers b, size_t np3, int nm, cudaStream_t s);
+// Tiles of 64 x 2^tshift x 2^tshift cells (tshift 0 ... 3, nm a multiple of 2^tshift); after the
+// sort, cnt[b] is the end of bucket b in the new order (tile t = buckets t 4^tshift ... + 4^tshift - 1).
+bool sort_tshift_ok(int nm, int tshift);
+cudaError_t launch_sort(SortBuffers b, size_t np3, int nm, int tshift, cudaStream_t s);
+// Deposit of particles ordered by tile (the last sort with this tshift; bucket ends in `ends`): each
+// tile plus its +1 halo accumulated in shared memory, then added to rho; corners outside go straight
+// to rho.
+cudaError_t launch_deposit_tiles(const float4* pos, int nm, int tshift, const unsigned* ends, unsigned long long* rho,
+                                 cudaStream_t s);
 // The _o arrays receive the particles in particle-id order (slot id[p] <- slot p), id_o the identity.
 cudaError_t launch_unsort(SortBuffers b, size_t np3, cudaStream_t s);
 cudaError_t launch_iota(int* id, size_t n, cudaStream_t s);

@@ -65,6 +65,71 @@ __global__ void k_deposit(const float4* __restrict__ pos, size_t np3, int nm, un
     deposit_corner(pos, p, (int)(t & 1), nm, rho);
 }
 
+// Tiled deposit of particles ordered by tile (a sort with the same tile shape): a CTA takes the
+// particles that were in tile (x0 .. x0 + TX - 1, y0 .. + T - 1, z0 .. + T - 1) at the last sort
+// and adds their corners that fall in the tile or its +1 halo (TX + 1) x (T + 1) x (T + 1) into
+// shared memory with 64-bit shared atomics; corners of particles that have moved further since
+// go straight to the mesh. The region is then added to the mesh cell by cell (consecutive x per
+// warp, zeros skipped), so where several particles share cells one global atomic serves them all.
+// Integer sums: the mesh is the same, bit for bit, as the one-atomic-per-corner deposit.
+constexpr int DT_T = 256;
+
+template <int TS>
+__global__ void __launch_bounds__(DT_T) k_deposit_tiles(const float4* __restrict__ pos, int nm, int xs,
+                                                        const unsigned* __restrict__ ends, unsigned ntiles,
+                                                        unsigned long long* __restrict__ rho) {
+    constexpr int T = 1 << TS, RY = T + 1, RXMAX = 65;
+    __shared__ unsigned long long acc[RXMAX * RY * RY];
+    const int RX = (1 << xs) + 1, NR = RX * RY * RY;
+    const int nbx = nm >> xs, nty = nm >> TS;
+    for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx = (int)(tile % (unsigned)nbx), ty = (int)((tile / (unsigned)nbx) % (unsigned)nty),
+                  tz = (int)(tile / ((unsigned)nbx * (unsigned)nty));
+        const int x0 = tx << xs, y0 = ty << TS, z0 = tz << TS;
+        const size_t b0 = (size_t)tile << (2 * TS);
+        const size_t start = tile == 0 ? 0 : ends[b0 - 1], end = ends[b0 + ((size_t)1 << (2 * TS)) - 1];
+        for (int i = threadIdx.x; i < NR; i += DT_T) acc[i] = 0ull;
+        __syncthreads();
+        for (size_t slot = start * 2 + threadIdx.x; slot < end * 2; slot += DT_T) {
+            const size_t p = slot >> 1;
+            const int dx = (int)(slot & 1);
+            const Cic c = cic_setup(pos[p], nm);
+            const unsigned long long wx = (unsigned long long)(dx ? c.fx : QONE - c.fx);
+            const unsigned long long wy[2] = {(unsigned long long)(QONE - c.fy), (unsigned long long)c.fy};
+            const unsigned long long wz[2] = {(unsigned long long)(QONE - c.fz), (unsigned long long)c.fz};
+            const int x = dx ? c.x1 : c.x0, ys[2] = {c.y0, c.y1}, zs[2] = {c.z0, c.z1};
+            int rx = x - x0;
+            if (rx < 0) rx += nm;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const unsigned long long w = wx * wy[dy] * wz[dz];
+                    if (!w) continue;
+                    int ry = ys[dy] - y0, rz = zs[dz] - z0;
+                    if (ry < 0) ry += nm;
+                    if (rz < 0) rz += nm;
+                    if (rx < RX && ry < RY && rz < RY)
+                        atomicAdd(&acc[(rz * RY + ry) * RX + rx], w);
+                    else
+                        atomicAdd(rho + ((size_t)zs[dz] * nm + ys[dy]) * nm + x, w);
+                }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < NR; i += DT_T) {
+            const unsigned long long v = acc[i];
+            if (!v) continue;
+            const int rx = i % RX, ry = (i / RX) % RY, rz = i / (RX * RY);
+            int gx = x0 + rx, gy = y0 + ry, gz = z0 + rz;
+            if (gx >= nm) gx -= nm;
+            if (gy >= nm) gy -= nm;
+            if (gz >= nm) gz -= nm;
+            atomicAdd(rho + ((size_t)gz * nm + gy) * nm + gx, v);
+        }
+        __syncthreads();   // the region is read before the next tile clears it
+    }
+}
+
 // Records the images of one particle that leave the past lightcone during the drift (§6): the image
 // x + R L (R in the step's replicate list) leaves when R_p <= R_L at a_i and R_p > R_L at a_{i+1};
 // its exit time interpolates both radii linearly (Eq. eq:lightconeinterp) and it is written at the
@@ -511,6 +576,23 @@ cudaError_t launch_gather_kick_drift(float4* pos, float* mom, const float* psi1,
     else
         k_gather_kick_drift<false><<<blocks(np3, block), block, 0, s>>>(pos, mom, psi1, psi2, force, np3, nm, c, drift,
                                                                         LightconeStep{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_tiles(const float4* pos, int nm, int tshift, const unsigned* ends, unsigned long long* rho,
+                                 cudaStream_t s) {
+    const int xs = sort_xshift(nm);
+    if (!sort_tshift_ok(nm, tshift) || tshift < 1 || xs > 6) return cudaErrorInvalidValue;
+    const unsigned ntiles = (unsigned)((size_t)(nm >> tshift) * (nm >> tshift) * (nm >> xs));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)sms * 8u < ntiles ? (unsigned)sms * 8u : ntiles;
+    switch (tshift) {
+        case 1: k_deposit_tiles<1><<<grid, DT_T, 0, s>>>(pos, nm, xs, ends, ntiles, rho); break;
+        case 2: k_deposit_tiles<2><<<grid, DT_T, 0, s>>>(pos, nm, xs, ends, ntiles, rho); break;
+        default: k_deposit_tiles<3><<<grid, DT_T, 0, s>>>(pos, nm, xs, ends, ntiles, rho); break;
+    }
     return cudaGetLastError();
 }
 

@@ -4,9 +4,12 @@
 // The deposit and the gather read and write the eight CIC corners of every particle. In particle-id
 // (Lagrangian) order a warp's particles start out as mesh neighbours, but as structure grows they
 // spread over more and more cache lines; with the arrays ordered by cell, a warp's corners are runs
-// of one or two mesh rows again. The order is a counting sort of the particles by bucket =
-// (z, y, x / XB) of their cell -- XB = 64 cells, so a bucket holds a few particles and the order
-// inside a bucket (which the scatter leaves to its atomics) changes nothing a warp reads.
+// of one or two mesh rows again. The order is a counting sort of the particles by bucket = one
+// x-run of XB = 64 cells (a bucket holds a few particles, and the order inside a bucket, which the
+// scatter leaves to its atomics, changes nothing a warp reads). The buckets are numbered tile by
+// tile: tiles of XB x T x T cells (T = 2^tshift, 1 by default) in (z, y, x) order, and inside a
+// tile its T x T runs by (z, y), so that the particles of one tile are contiguous and the bucket
+// ends of the sort delimit them (the tiled deposit accumulates a tile in shared memory).
 //
 // Every step of the method is per particle or an order-independent integer sum (the fixed-point
 // deposit), so the physics does not depend on the order; `id` keeps each slot's particle id for
@@ -21,10 +24,11 @@ constexpr int SCAN_T = 1024;           // threads of the scan kernels
 constexpr int SCAN_PER = 4;            // elements per thread in the block scan
 constexpr int SCAN_TILE = SCAN_T * SCAN_PER;
 
-__device__ __forceinline__ unsigned bucket_of(float w, int nm, int xshift) {
+__device__ __forceinline__ unsigned bucket_of(float w, int nm, int xshift, int tshift) {
     const unsigned c = __float_as_uint(w), u = (unsigned)nm;   // linear cell x + nm (y + nm z)
-    const unsigned x = c % u, yz = c / u;
-    return yz * (u >> xshift) + (x >> xshift);
+    const unsigned x = c % u, yz = c / u, y = yz % u, z = yz / u, m = (1u << tshift) - 1u;
+    const unsigned tile = ((z >> tshift) * (u >> tshift) + (y >> tshift)) * (u >> xshift) + (x >> xshift);
+    return (tile << (2 * tshift)) + ((z & m) << tshift) + (y & m);
 }
 
 // Warp-aggregated increment: the lanes of a warp with the same bucket (in particle order a warp's
@@ -40,10 +44,11 @@ __device__ __forceinline__ unsigned warp_bucket_add(unsigned* ctr, unsigned b) {
     return base + (unsigned)__popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void k_sort_count(const float4* __restrict__ pos, size_t np3, int nm, int xshift, unsigned* __restrict__ cnt) {
+__global__ void k_sort_count(const float4* __restrict__ pos, size_t np3, int nm, int xshift, int tshift,
+                             unsigned* __restrict__ cnt) {
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
-    warp_bucket_add(cnt, bucket_of(__ldg(&pos[p].w), nm, xshift));
+    warp_bucket_add(cnt, bucket_of(__ldg(&pos[p].w), nm, xshift, tshift));
 }
 
 // Exclusive scan of cnt[0..n) in tiles of SCAN_TILE: tile sums first, then the scan within tiles
@@ -152,14 +157,14 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const unsigned* cnt, size
 // Move every particle to the next free slot of its bucket (cursor[] starts at the bucket offsets).
 __global__ void k_sort_scatter(const float4* __restrict__ pos, const float* __restrict__ mom,
                                const float* __restrict__ psi1, const float* __restrict__ psi2,
-                               const int* __restrict__ id, size_t np3, int nm, int xshift,
+                               const int* __restrict__ id, size_t np3, int nm, int xshift, int tshift,
                                unsigned* __restrict__ cursor, float4* __restrict__ pos_o, float* __restrict__ mom_o,
                                float* __restrict__ psi1_o, float* __restrict__ psi2_o, int* __restrict__ id_o,
                                int* err) {
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
     const float4 P = __ldcs(pos + p);
-    const size_t d = warp_bucket_add(cursor, bucket_of(P.w, nm, xshift));
+    const size_t d = warp_bucket_add(cursor, bucket_of(P.w, nm, xshift, tshift));
     if (d >= np3) {   // cannot happen with consistent counts; guards the writes below
         atomicOr(err, 8);
         return;
@@ -211,16 +216,19 @@ size_t sort_buckets(int nm) { return (size_t)nm * nm * (size_t)(nm >> sort_xshif
 
 size_t sort_tiles(int nm) { return (sort_buckets(nm) + SCAN_TILE - 1) / SCAN_TILE; }
 
-cudaError_t launch_sort(SortBuffers b, size_t np3, int nm, cudaStream_t s) {
+bool sort_tshift_ok(int nm, int tshift) { return tshift >= 0 && tshift <= 3 && nm % (1 << tshift) == 0; }
+
+cudaError_t launch_sort(SortBuffers b, size_t np3, int nm, int tshift, cudaStream_t s) {
+    if (!sort_tshift_ok(nm, tshift)) return cudaErrorInvalidValue;
     const int xs = sort_xshift(nm);
     const size_t nb = sort_buckets(nm), nt = sort_tiles(nm);
     cudaError_t e = cudaMemsetAsync(b.cnt, 0, nb * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    k_sort_count<<<blocks(np3, 256), 256, 0, s>>>(b.pos, np3, nm, xs, b.cnt);
+    k_sort_count<<<blocks(np3, 256), 256, 0, s>>>(b.pos, np3, nm, xs, tshift, b.cnt);
     k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, s>>>(b.cnt, nb, b.tile_sum);
     k_scan_sums<<<1, SCAN_T, 0, s>>>(b.tile_sum, (int)nt);
     k_scan_apply<<<(unsigned)nt, SCAN_T, 0, s>>>(b.cnt, nb, b.tile_sum, b.cnt);   // counts -> cursors in place
-    k_sort_scatter<<<blocks(np3, 256), 256, 0, s>>>(b.pos, b.mom, b.psi1, b.psi2, b.id, np3, nm, xs, b.cnt, b.pos_o,
+    k_sort_scatter<<<blocks(np3, 256), 256, 0, s>>>(b.pos, b.mom, b.psi1, b.psi2, b.id, np3, nm, xs, tshift, b.cnt, b.pos_o,
                                                      b.mom_o, b.psi1_o, b.psi2_o, b.id_o, b.err);
     return cudaGetLastError();
 }

@@ -417,15 +417,18 @@ def test_finalize_adds_lpt_momentum(C):
 
 # --- particle order ------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("np_,nm,every", [(32, 64, 1), (64, 128, 3), (32, 96, 2)])
-def test_cell_order_changes_no_result(C, np_, nm, every):
-    """Reordering the particle arrays by cell is invisible: every step is per particle or an exact
-    integer sum, so runs with and without it give bit-identical catalogues, states, LPT fields,
-    densities, spectra and finalized momenta, in particle-id order."""
+@pytest.mark.parametrize("np_,nm,every,tiles", [(32, 64, 1, 0), (64, 128, 3, 0), (32, 96, 2, 0), (32, 64, 1, 2),
+                                                 (64, 128, 1, 4), (64, 128, 2, 8), (32, 96, 1, 4)])
+def test_cell_order_changes_no_result(C, np_, nm, every, tiles):
+    """Reordering the particle arrays by cell (by rows, or tile by tile with the tiled deposit) is
+    invisible: every step is per particle or an exact integer sum, so runs with and without it give
+    bit-identical catalogues, states, LPT fields, densities, spectra and finalized momenta, in
+    particle-id order."""
     kw = dict(np=np_, nm=nm, box=200.0, seed=13, n_steps=6)
     a, b = Sim(C, **kw), Sim(C, **kw)
     try:
         C.colapm_set_sort(b.ctx, every)
+        C.colapm_set_deposit_tiles(b.ctx, tiles)
         for s in (a, b):
             C.colapm_make_ics(s.ctx)
             C.colapm_step(s.ctx, 4)
@@ -457,6 +460,33 @@ def test_cell_order_changes_no_result(C, np_, nm, every):
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("tiles", [0, 2, 4, 8])
+def test_tiled_deposit_bit_exact_on_clustered_state(C, tiles):
+    """The tiled deposit (each tile and its halo summed in shared memory) on a clustered state in
+    tile order, right after the sort and after particles have moved out of their tiles: the int64
+    mesh equals the oracle's deposit of the same positions exactly."""
+    np_, nm = 64, 128
+    s = Sim(C, np=np_, nm=nm, box=200.0, seed=3, n_steps=6)
+    try:
+        C.colapm_set_sort(s.ctx, 1)
+        C.colapm_set_deposit_tiles(s.ctx, tiles)
+        assert C.colapm_get_config(s.ctx)["deposit_tiles"] == tiles
+        C.colapm_make_ics(s.ctx)
+        C.colapm_step(s.ctx, 1)
+        cell, off, _ = workloads.clustered_state(np_, nm, 17)
+        C.colapm_set_state(s.ctx, cell, off, None)
+        for _ in range(2):
+            C.colapm_step(s.ctx, 1)             # reorders (tile key) before the step, then moves the particles
+            gpu = s.density()                   # deposit of the moved particles, still in tile order
+            cell2, off2, _ = s.state()
+            assert np.array_equal(gpu, opm.cic_deposit(mesh_coords(cell2, off2), nm))
+        for bad in (3, 16, -2):
+            with pytest.raises(C.ColapmError):
+                C.colapm_set_deposit_tiles(s.ctx, bad)
+    finally:
+        s.close()
 
 
 def test_cell_order_checkpoint_and_async_export(C):
