@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-study", action="store_true")
     ap.add_argument("--sort", type=int, default=None,
                     help="reorder the particles by cell every K steps (profiling aid; the default is the library's)")
+    ap.add_argument("--sort-tiles", type=int, default=None,
+                    help="order of the reordering: tiles of 64 x T x T cells, T in 1, 2, 4, 8 (profiling aid)")
     ap.add_argument("--deposit-tiles", type=int, default=None,
                     help="deposit tiles of 64 x T x T cells, T in 0, 2, 4, 8 (profiling aid; the default is the library's)")
     ap.add_argument("--engine", default="default", choices=["default", "fused", "two_stage", "stockham"],
@@ -448,6 +450,8 @@ def main():
         C.colapm_set_engine(ctx, fused, two, 256)
     if args.sort is not None:
         C.colapm_set_sort(ctx, args.sort)
+    if args.sort_tiles is not None:
+        C.colapm_set_sort_tiles(ctx, args.sort_tiles)
     if args.deposit_tiles is not None:
         C.colapm_set_deposit_tiles(ctx, args.deposit_tiles)
     nbins = 100

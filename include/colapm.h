@@ -297,12 +297,12 @@ long long colapm_kernel_launches(const colapm_ctx* ctx);
  *      (128, 256, 512);
  *   2. then, unless the fused passes won, the radix plan of each pass (COLAPM_PLAN_* bits) in
  *      turn: a pass switched to the other plan is kept if the step gets faster;
- *   3. where the context reorders its particles (colapm_set_sort), the deposit tile shape
- *      (colapm_set_deposit_tiles: 0, 2, 4, 8): the particles are sorted with each shape's key and
- *      the deposit alone is timed.
- * Each candidate of 1 and 2 is one force computation and gather from the same state (fastest of
- * three after a warm-up); the particle state and step counter are then restored, and step 3 leaves
- * the particles in the order of the shape kept (no result depends on the order). Requires initial conditions
+ *   3. where the context reorders its particles (colapm_set_sort), the tile shape of the sort key
+ *      (colapm_set_sort_tiles: 1, 2, 4, 8) and, for tiles, the tiled or the plain deposit
+ *      (colapm_set_deposit_tiles): the particles are sorted with each key.
+ * Each candidate is one force computation and gather from the same state (fastest of three after a
+ * warm-up); the particle state and step counter are then restored, except that step 3 leaves the
+ * particles in the order of the key kept (no result depends on the order). Requires initial conditions
  * (COLAPM_E_STATE). Synchronises. `choice` (may be NULL, else 3 ints) receives {1 if every pass is
  * two-stage else 0, block, fused x-y passes (0 or 3)}; colapm_get_config gives the whole choice. */
 int colapm_autotune(colapm_ctx* ctx, int* choice);
@@ -319,8 +319,9 @@ int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
  * uses the plain layout there. COLAPM_E_ARG outside 0 ... COLAPM_PLAN_ALL. */
 int colapm_set_plan(colapm_ctx* ctx, int plan);
 
-/* The context's configuration: cfg (5 ints) = {plan mask, particle-kernel block size, fused x-y
- * passes (0 where N_m has none), sort cadence (colapm_set_sort), deposit tile T (0: none)}. */
+/* The context's configuration: cfg (6 ints) = {plan mask, particle-kernel block size, fused x-y
+ * passes (0 where N_m has none), sort cadence (colapm_set_sort), sort-key tile T (1: rows),
+ * tiled deposit (0/1)}. */
 int colapm_get_config(const colapm_ctx* ctx, int* cfg);
 
 /* Reorder the particle arrays by mesh cell before every `every`-th step (0: never). The default is
@@ -333,15 +334,24 @@ int colapm_get_config(const colapm_ctx* ctx, int* cfg);
  * COLAPM_E_ARG for every < 0. */
 int colapm_set_sort(colapm_ctx* ctx, int every);
 
+/* Order of the reordering: runs of 64 cells along x numbered tile by tile, tiles of 64 x T x T
+ * cells (T = 1, 2, 4 or 8, N_m a multiple of T; 1 is plain rows; the default is 2, which measured
+ * fastest for the gather and the sort itself at 1024^3): the particles of a tile are then
+ * contiguous. COLAPM_E_ARG for other T. Takes effect at the next reordering; T = 1
+ * also turns the tiled deposit off. */
+int colapm_set_sort_tiles(colapm_ctx* ctx, int t);
+
 /* Deposit tiles of 64 x T x T cells (T = 2, 4 or 8, N_m a multiple of T; 0: none, the default).
- * The reordering then sorts the particles tile by tile (inside a tile by runs of 64 cells along x),
- * and while they are in that order the deposit gives each tile's particles to one CTA, which adds
+ * Sets the sort key's tiles to T (colapm_set_sort_tiles), and while the particles are in that
+ * order the deposit gives each tile's particles to one CTA, which adds
  * their corners inside the tile and its +1 halo into shared memory with 64-bit shared atomics and
  * then adds the (T + 1)^2 x 65 region to the mesh, one atomic per non-zero cell; corners of
  * particles that moved out of that region since the sort go straight to the mesh. The mesh is the
  * same integer sum bit for bit (the analogue of the paper's per-rank density slab, §4: each tile is
- * summed where its particles are, then added into the global mesh). Takes effect at the next
- * reordering. COLAPM_E_ARG for other T. */
+ * summed where its particles are, then added into the global mesh). It pays where many
+ * particles share cells; at 1/8 particle per cell (N_m = 2 N_p) it measured slower than the plain
+ * deposit. Takes effect at the next reordering; 0 turns it off (the sort key stays). COLAPM_E_ARG
+ * for other T. */
 int colapm_set_deposit_tiles(colapm_ctx* ctx, int t);
 
 /* ---- batched mocks (many independent realisations of uneven sizes) ----------------------- */

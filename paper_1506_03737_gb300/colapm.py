@@ -95,6 +95,7 @@ def _load():
         "colapm_get_config": (I, [P, P]),
         "colapm_set_sort": (I, [P, I]),
         "colapm_set_deposit_tiles": (I, [P, I]),
+        "colapm_set_sort_tiles": (I, [P, I]),
         "colapm_batch_create": (I, [I, P, I, P, ctypes.POINTER(P)]),
         "colapm_batch_run": (I, [P, P, I, D, D, P, P, P]),
         "colapm_batch_streams": (I, [P]),
@@ -344,10 +345,14 @@ def colapm_set_plan(ctx, plan):
 
 
 def colapm_get_config(ctx):
-    cfg = np.zeros(5, dtype=np.int32)
+    cfg = np.zeros(6, dtype=np.int32)
     _check(LIB.colapm_get_config(ctx, _ptr(cfg)), "colapm_get_config")
     return {"plan": int(cfg[0]), "block": int(cfg[1]), "fused": int(cfg[2]), "sort_every": int(cfg[3]),
-            "deposit_tiles": int(cfg[4])}
+            "sort_tiles": int(cfg[4]), "deposit_tiled": bool(cfg[5])}
+
+
+def colapm_set_sort_tiles(ctx, t):
+    _check(LIB.colapm_set_sort_tiles(ctx, int(t)), "colapm_set_sort_tiles")
 
 
 def colapm_set_deposit_tiles(ctx, t):

@@ -37,7 +37,8 @@ struct colapm_ctx {
     unsigned* sort_cnt = nullptr;        // bucket counters / cursors of the cell sort
     unsigned* sort_tile = nullptr;       // their tile sums
     int sort_every = 0;                  // reorder by cell before every k-th step (0: never)
-    int dep_tshift = 0;                  // sort key and deposit: tiles of 64 x 2^t x 2^t cells (0: rows, plain deposit)
+    int key_tshift = 0;                  // sort key: tiles of 64 x 2^t x 2^t cells (0: rows of 64)
+    bool dep_tiled = false;              // tiled deposit while the particles are in tile order
     int sorted_tshift = -1;              // tile shift of the order the particles are in (-1: id order)
     double fnl = 0.0;                    // local primordial non-Gaussianity of the next ICs
     float* fnl_tab = nullptr;            // per |n|^2 of the IC grid: 1 / (M N^3), then M (colapm_set_fnl)
@@ -197,14 +198,16 @@ DepositSrc own_particles(const colapm_ctx* c) {
 // Fixed-point CIC deposit into c's mesh of the given particles (default: c's own).
 // Whether the own particles are ordered by the tiles of the tiled deposit (the last sort used the
 // context's tile shape and nothing has restored id order since).
-bool tiles_ready(const colapm_ctx* c) { return c->dep_tshift > 0 && !c->id_order && c->sorted_tshift == c->dep_tshift; }
+bool tiles_ready(const colapm_ctx* c) {
+    return c->dep_tiled && c->key_tshift > 0 && !c->id_order && c->sorted_tshift == c->key_tshift;
+}
 
 int deposit(colapm_ctx* c, const DepositSrc* src = nullptr) {
     Phase ph(c, COLAPM_PHASE_DEPOSIT);
     if (!c->rho_clean) CK(cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), c->stream));
     c->rho_clean = false;
     if (!src && tiles_ready(c)) {
-        CKL(launch_deposit_tiles(c->pos, c->nm, c->dep_tshift, c->sort_cnt, c->rho, c->stream));
+        CKL(launch_deposit_tiles(c->pos, c->nm, c->key_tshift, c->sort_cnt, c->rho, c->stream));
         return COLAPM_OK;
     }
     const DepositSrc d = src ? *src : own_particles(c);
@@ -245,10 +248,10 @@ void swap_particle_arrays(colapm_ctx* c) {
 // Reorder the particle arrays by mesh cell (counting sort into the second set, then swap).
 int sort_particles(colapm_ctx* c) {
     Phase ph(c, COLAPM_PHASE_SORT);
-    CKL(launch_sort(sort_buffers(c), c->np3, c->nm, c->dep_tshift, c->stream));
+    CKL(launch_sort(sort_buffers(c), c->np3, c->nm, c->key_tshift, c->stream));
     swap_particle_arrays(c);
     c->id_order = false;
-    c->sorted_tshift = c->dep_tshift;
+    c->sorted_tshift = c->key_tshift;
     return COLAPM_OK;
 }
 
@@ -473,7 +476,8 @@ const char* colapm_strerror(int code) {
 static std::mutex g_tune_mu;
 struct Tuned {
     unsigned plan;
-    int fused, block, dep_tshift;
+    int fused, block, key_tshift;
+    bool dep_tiled;
 };
 static std::map<std::pair<int, int>, Tuned> g_tuned;   // (np, nm) -> choice
 
@@ -548,6 +552,7 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
     // 1024^3 one sort before step 5 of 10 measured 28.7 against 29.1 ms per step; more frequent sorts
     // cost more than they save, see colapm_set_sort).
     c->sort_every = c->nm >= 512 && p->n_steps >= 4 ? p->n_steps / 2 : 0;
+    c->key_tshift = c->nm % 2 == 0 ? 1 : 0;   // tiles of 64 x 2 x 2 cells (measured best of 1, 2, 4, 8 at 1024^3)
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find({c->np, c->nm});
@@ -555,7 +560,8 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
             c->plan = it->second.plan;
             c->fused = it->second.fused;
             c->block = it->second.block;
-            c->dep_tshift = it->second.dep_tshift;
+            c->key_tshift = it->second.key_tshift;
+            c->dep_tiled = it->second.dep_tiled;
         }
     }
     *out = c;
@@ -1245,16 +1251,37 @@ int colapm_get_config(const colapm_ctx* c, int* cfg) {
     cfg[1] = c->block;
     cfg[2] = c->xy_ring ? c->fused : 0;
     cfg[3] = c->sort_every;
-    cfg[4] = c->dep_tshift > 0 ? 1 << c->dep_tshift : 0;
+    cfg[4] = 1 << c->key_tshift;
+    cfg[5] = c->dep_tiled ? 1 : 0;
+    return COLAPM_OK;
+}
+
+// t = 2^ts with 0 <= ts <= 3 and nm a multiple of t; -1 otherwise.
+static int tile_shift_of(const colapm_ctx* c, int t) {
+    for (int ts = 0; ts <= 3; ++ts)
+        if (t == (1 << ts)) return sort_tshift_ok(c->nm, ts) ? ts : -1;
+    return -1;
+}
+
+int colapm_set_sort_tiles(colapm_ctx* c, int t) {
+    if (!c) return COLAPM_E_ARG;
+    const int ts = tile_shift_of(c, t);
+    if (ts < 0) return COLAPM_E_ARG;
+    c->key_tshift = ts;
+    if (ts == 0) c->dep_tiled = false;
     return COLAPM_OK;
 }
 
 int colapm_set_deposit_tiles(colapm_ctx* c, int t) {
     if (!c) return COLAPM_E_ARG;
-    int ts = 0;
-    while (ts < 3 && (1 << ts) < t) ++ts;
-    if (t != 0 && (t != (1 << ts) || ts < 1 || !sort_tshift_ok(c->nm, ts))) return COLAPM_E_ARG;
-    c->dep_tshift = t == 0 ? 0 : ts;
+    if (t == 0) {
+        c->dep_tiled = false;
+        return COLAPM_OK;
+    }
+    const int ts = tile_shift_of(c, t);
+    if (ts < 1) return COLAPM_E_ARG;
+    c->key_tshift = ts;
+    c->dep_tiled = true;
     return COLAPM_OK;
 }
 
@@ -1365,35 +1392,46 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     c->plan = best_p;
     c->fused = best_f;
     c->block = best_b;
-    // 3. the deposit tile shape, where the context reorders its particles: for each shape the
-    //    particles are sorted with its key (the order changes no result) and the deposit is timed
-    //    alone; the particles are left in the order of the shape kept
-    int best_t = c->dep_tshift;
-    if (c->sort_every > 0) {
-        float best_dep = 1e30f;
+    // 3. where the context reorders its particles: the tile shape of the sort key (rows of 64
+    //    cells, or tiles of 64 x T x T) and, for tiles, the tiled deposit or the plain one. For each
+    //    candidate the particles are sorted with its key (the order changes no result), and one force
+    //    computation + gather is timed from that state as in 1 (restored after each repetition);
+    //    the particles are left in the order of the candidate kept
+    int best_k = c->key_tshift;
+    bool best_dt = c->dep_tiled;
+    if (c->sort_every > 0 && r == COLAPM_OK) {
+        float best3 = 1e30f;
         for (int ts = 0; ts <= 3 && r == COLAPM_OK; ++ts) {
-            if (ts > 0 && !sort_tshift_ok(c->nm, ts)) continue;
-            c->dep_tshift = ts;
+            if (!sort_tshift_ok(c->nm, ts)) continue;
+            c->key_tshift = ts;
+            c->dep_tiled = false;
             r = sort_particles(c);
-            float ms_best = 1e30f;
-            for (int rep = 0; rep < 4 && r == COLAPM_OK; ++rep) {
-                cudaEventRecord(e0, c->stream);
-                r = deposit(c);
-                cudaEventRecord(e1, c->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) r = COLAPM_E_CUDA;
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0 && ms < ms_best) ms_best = ms;
+            if (r != COLAPM_OK) break;
+            if (cudaMemcpyAsync(snap, c->pos, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(snap + 4 * c->np3, c->mom, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                c->stream) != cudaSuccess) {
+                r = COLAPM_E_CUDA;
+                break;
             }
-            if (ms_best < best_dep) {
-                best_dep = ms_best;
-                best_t = ts;
+            for (int dt = 0; dt < (ts > 0 ? 2 : 1) && r == COLAPM_OK; ++dt) {
+                c->dep_tiled = dt == 1;
+                const float ms = trial(best_p, best_f, best_b);
+                if (ms < best3) {
+                    best3 = ms;
+                    best_k = ts;
+                    best_dt = dt == 1;
+                }
             }
+            cudaMemcpyAsync(c->pos, snap, c->np3 * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync(c->mom, snap + 4 * c->np3, 3 * c->np3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
         }
-        if (r == COLAPM_OK && c->dep_tshift != best_t) {
-            c->dep_tshift = best_t;
+        c->dep_tiled = best_dt;
+        if (r == COLAPM_OK && c->key_tshift != best_k) {
+            c->key_tshift = best_k;
             r = sort_particles(c);
         }
+        c->step = step0;
+        c->finalized = fin0;
         if (r == COLAPM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) r = COLAPM_E_CUDA;
     }
     cudaEventDestroy(e0);
@@ -1401,7 +1439,7 @@ int colapm_autotune(colapm_ctx* c, int* choice) {
     if (r != COLAPM_OK) return r;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[{c->np, c->nm}] = Tuned{best_p, best_f, best_b, best_t};
+        g_tuned[{c->np, c->nm}] = Tuned{best_p, best_f, best_b, best_k, best_dt};
     }
     if (choice) {
         choice[0] = best_p == COLAPM_PLAN_ALL ? 1 : 0;

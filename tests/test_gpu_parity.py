@@ -418,7 +418,7 @@ def test_finalize_adds_lpt_momentum(C):
 # --- particle order ------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("np_,nm,every,tiles", [(32, 64, 1, 0), (64, 128, 3, 0), (32, 96, 2, 0), (32, 64, 1, 2),
-                                                 (64, 128, 1, 4), (64, 128, 2, 8), (32, 96, 1, 4)])
+                                                 (64, 128, 1, 4), (64, 128, 2, 8), (32, 96, 1, 4), (64, 128, 1, -4)])
 def test_cell_order_changes_no_result(C, np_, nm, every, tiles):
     """Reordering the particle arrays by cell (by rows, or tile by tile with the tiled deposit) is
     invisible: every step is per particle or an exact integer sum, so runs with and without it give
@@ -428,7 +428,10 @@ def test_cell_order_changes_no_result(C, np_, nm, every, tiles):
     a, b = Sim(C, **kw), Sim(C, **kw)
     try:
         C.colapm_set_sort(b.ctx, every)
-        C.colapm_set_deposit_tiles(b.ctx, tiles)
+        if tiles < 0:
+            C.colapm_set_sort_tiles(b.ctx, -tiles)     # tile-major order, plain deposit
+        else:
+            C.colapm_set_deposit_tiles(b.ctx, tiles)
         for s in (a, b):
             C.colapm_make_ics(s.ctx)
             C.colapm_step(s.ctx, 4)
@@ -472,7 +475,8 @@ def test_tiled_deposit_bit_exact_on_clustered_state(C, tiles):
     try:
         C.colapm_set_sort(s.ctx, 1)
         C.colapm_set_deposit_tiles(s.ctx, tiles)
-        assert C.colapm_get_config(s.ctx)["deposit_tiles"] == tiles
+        cfg = C.colapm_get_config(s.ctx)
+        assert cfg["deposit_tiled"] == (tiles > 0) and cfg["sort_tiles"] == max(tiles, 1)
         C.colapm_make_ics(s.ctx)
         C.colapm_step(s.ctx, 1)
         cell, off, _ = workloads.clustered_state(np_, nm, 17)
@@ -482,9 +486,12 @@ def test_tiled_deposit_bit_exact_on_clustered_state(C, tiles):
             gpu = s.density()                   # deposit of the moved particles, still in tile order
             cell2, off2, _ = s.state()
             assert np.array_equal(gpu, opm.cic_deposit(mesh_coords(cell2, off2), nm))
-        for bad in (3, 16, -2):
+        for bad in (3, 16, -2, 1):
             with pytest.raises(C.ColapmError):
                 C.colapm_set_deposit_tiles(s.ctx, bad)
+        for bad in (0, 3, 16):
+            with pytest.raises(C.ColapmError):
+                C.colapm_set_sort_tiles(s.ctx, bad)
     finally:
         s.close()
 
