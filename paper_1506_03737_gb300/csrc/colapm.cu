@@ -69,6 +69,7 @@ struct colapm_ctx {
     int* pw_bin = nullptr;               // |n|^2 thresholds of the bins
     double* pw_acc = nullptr;            // ksum[nb], psum[nb], cnt[nb] (as u64)
     int pw_n2cap = 0, pw_nbcap = 0;
+    float pw_lga = 0.0f, pw_lgb = 0.0f;  // log-spacing guess of the bins (PowerArgs)
     unsigned long long* d_seed = nullptr;          // device seed of the Gaussian field
     const unsigned long long* seed_src = nullptr;  // the seed the ICs read (own, or a batch slot)
     unsigned plan = COLAPM_PLAN_ALL;     // passes on the two-stage register FFT, else Stockham (autotuned)
@@ -710,6 +711,9 @@ int power_prepare(colapm_ctx* c, int nbins, double kmin, double kmax) {
     }
     CK(cudaMemcpyAsync(c->pw_bin, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    const double lr = std::log2(kmax / kmin);
+    c->pw_lga = (float)(0.5 * nbins / lr);
+    c->pw_lgb = (float)(nbins * std::log2(kf / kmin) / lr);
     return COLAPM_OK;
 }
 
@@ -740,6 +744,8 @@ int power_enqueue(colapm_ctx* c, int nbins, const DepositSrc* src = nullptr, boo
     pw.nbins = nbins;
     const double nm = c->nm;
     pw.pnorm = (float)(box * box * box / (nm * nm * nm * nm * nm * nm));
+    pw.lga = c->pw_lga;
+    pw.lgb = c->pw_lgb;
     CKL(launch_fz(c->nm, Z_POWER, reinterpret_cast<float2*>(c->F), ZOut{}, c->tw_m, c->sinc2_m + (window ? 0 : c->nm), 0, 1.0f, &pw,
                   c->stream, ts(c, COLAPM_PLAN_Z), use_blocked(c)));
     return COLAPM_OK;

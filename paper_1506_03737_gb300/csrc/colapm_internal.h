@@ -47,7 +47,22 @@ struct PowerArgs {
     int nbins;
     float kf;                   // 2 pi / L (h/Mpc)
     float pnorm;                // L^3 / N^6
+    // first guess of the bin of |n|^2 for log-spaced bins, floor(lga log2 |n|^2 + lgb), corrected
+    // against n2_lo (lga = 0: binary search only)
+    float lga, lgb;
 };
+
+// Guess from the log-spacing of the bins (at most one or two off near an edge), then a walk to
+// the bin whose thresholds hold |n|^2; -1 outside. The same bin as the binary search.
+__device__ __forceinline__ int power_bin_guess(int n2, const int* lo, const PowerArgs& pw) {
+    const int nb = pw.nbins;
+    if (n2 < lo[0] || n2 >= lo[nb]) return -1;
+    int b = (int)floorf(fmaf(pw.lga, __log2f((float)n2), pw.lgb));
+    b = b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
+    while (b > 0 && n2 < lo[b]) --b;
+    while (b < nb - 1 && n2 >= lo[b + 1]) ++b;
+    return b;
+}
 
 // Bin of |n|^2 given the thresholds (binary search; -1 outside).
 __device__ __forceinline__ int power_bin(int n2, const int* lo, int nbins) {
@@ -58,6 +73,55 @@ __device__ __forceinline__ int power_bin(int n2, const int* lo, int nbins) {
         if (lo[m] <= n2) a = m; else b = m;
     }
     return a;
+}
+
+// Bins the modes (nx, ny, nz(z)) of one column for z = z0 ... z0 + per - 1 (ny not on the Nyquist
+// plane; z = L/2 skipped) into the FP64 bins: FP32 sums over runs of consecutive modes in one bin
+// (a few dozen at most), added to the bin when the run leaves it. The current bin's |n|^2 range
+// stays in registers, so a mode of the same bin costs two compares; a new bin comes from the
+// log-spacing guess (power_bin_guess) or the binary search. value(z) gives the mode's complex
+// amplitude, sinc2[z] the CIC window factor along z (wxy the product of the x and y factors).
+template <typename F>
+__device__ __forceinline__ void bin_column_run(int nx, int ny, int z0, int per, int L, float wxy,
+                                               const float* __restrict__ sinc2, const int* lo, const PowerArgs& pw,
+                                               double* psum, double* ksum, unsigned long long* cnt, F value) {
+    const float mult = nx == 0 ? 1.0f : 2.0f;
+    const float cp = mult * pw.pnorm, ck = mult * pw.kf;
+    const unsigned ci = nx == 0 ? 1u : 2u;
+    const int nxy2 = nx * nx + ny * ny;
+    int rb = -1, blo = 0, bhi = 0;
+    float rp = 0.0f, rk = 0.0f;
+    unsigned rc = 0;
+    for (int zz = 0; zz < per; ++zz) {
+        const int z = z0 + zz;
+        if (z == L / 2) continue;
+        const int nz = z < L / 2 ? z : z - L;
+        const int n2 = nxy2 + nz * nz;
+        if (n2 < blo || n2 >= bhi) {   // the run leaves its bin
+            if (rb >= 0) {
+                atomicAdd(&psum[rb], (double)rp);
+                atomicAdd(&ksum[rb], (double)rk);
+                atomicAdd(&cnt[rb], (unsigned long long)rc);
+            }
+            rp = 0.0f;
+            rk = 0.0f;
+            rc = 0;
+            rb = n2 == 0 ? -1 : (pw.lga != 0.0f ? power_bin_guess(n2, lo, pw) : power_bin(n2, lo, pw.nbins));
+            blo = rb >= 0 ? lo[rb] : n2;        // outside every bin: a range of this |n|^2 alone
+            bhi = rb >= 0 ? lo[rb + 1] : n2 + 1;
+        }
+        if (rb < 0) continue;
+        const float2 v = value(z);
+        const float w = wxy * sinc2[z];
+        rp += __fdividef(cp * (v.x * v.x + v.y * v.y), w * w);
+        rk += ck * sqrtf((float)n2);
+        rc += ci;
+    }
+    if (rb >= 0) {
+        atomicAdd(&psum[rb], (double)rp);
+        atomicAdd(&ksum[rb], (double)rk);
+        atomicAdd(&cnt[rb], (unsigned long long)rc);
+    }
 }
 
 // --- launchers (fft_kernels_*.cu) ----------------------------------------------------------

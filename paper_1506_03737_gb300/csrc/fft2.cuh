@@ -288,50 +288,18 @@ __global__ void __launch_bounds__(Z2<L, MODE, C, DIRECT>::T, Z2<L, MODE, C, DIRE
         }
 
         if constexpr (MODE == Z_POWER) {
-            // Store the spectrum of the 8 columns in z order, then let each thread bin a run of
-            // consecutive z of one column, flushing when the bin changes.
+            // Store the spectrum of the C columns in z order, then bin runs of consecutive z.
             if (tid < TB) {
 #pragma unroll
                 for (int r = 0; r < R2; ++r) xb[Xch<L, R1, C>::at(c, j + R1 * r)] = v[r];
             }
             __syncthreads();
-            constexpr int PER = L * C / T;
-            const int pc = tid % C, z0 = (tid / C) * PER, px = kx0 + pc;
-            if (!nyq_y) {
-                int rb = -1;
-                float rp = 0.0f, rk = 0.0f;   // FP32 sums over one run of at most a few dozen modes, flushed to FP64 bins
-                unsigned rc = 0;
-                const float mult = px == 0 ? 1.0f : 2.0f;   // conjugate twin with k_x -> -k_x
-#pragma unroll 8
-                for (int zz = 0; zz < PER; ++zz) {
-                    const int z = z0 + zz;
-                    if (z == L / 2) continue;
-                    const int nz = sbin(z, L);
-                    const int n2 = px * px + ny * ny + nz * nz;
-                    const int b = n2 == 0 ? -1 : (rb >= 0 && n2 >= lo[rb] && n2 < lo[rb + 1]) ? rb : power_bin(n2, lo, pw.nbins);
-                    if (b < 0) continue;
-                    if (b != rb) {
-                        if (rb >= 0) {
-                            atomicAdd(&psum[rb], (double)rp);
-                            atomicAdd(&ksum[rb], (double)rk);
-                            atomicAdd(&cnt[rb], (unsigned long long)rc);
-                        }
-                        rb = b;
-                        rp = 0.0f;
-                        rk = 0.0f;
-                        rc = 0;
-                    }
-                    const float2 q = xb[Xch<L, R1, C>::at(pc, z)];
-                    const float w = sinc2[px] * sinc2[ky] * sinc2[z];
-                    rp += __fdividef(mult * (q.x * q.x + q.y * q.y) * pw.pnorm, w * w);
-                    rk += mult * pw.kf * sqrtf((float)n2);
-                    rc += px == 0 ? 1u : 2u;
-                }
-                if (rb >= 0) {
-                    atomicAdd(&psum[rb], (double)rp);
-                    atomicAdd(&ksum[rb], (double)rk);
-                    atomicAdd(&cnt[rb], (unsigned long long)rc);
-                }
+
+            if (!nyq_y) {   // each thread a run of consecutive z of one column
+                constexpr int PER = L * C / T;
+                const int pc = tid % C;
+                bin_column_run(kx0 + pc, ny, (tid / C) * PER, PER, L, sinc2[kx0 + pc] * sinc2[ky], sinc2, lo, pw, psum,
+                               ksum, cnt, [&](int z) { return xb[Xch<L, R1, C>::at(pc, z)]; });
             }
             __syncthreads();
             continue;

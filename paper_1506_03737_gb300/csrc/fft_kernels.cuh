@@ -388,43 +388,11 @@ __global__ void __launch_bounds__(TCfg<L>::T) k_fz(float2* __restrict__ in, ZOut
 
         if constexpr (MODE == Z_POWER) {
             // Each thread bins a run of consecutive z of one column, flushing when the bin changes.
-            constexpr int PER = L * 8 / T;
-            const int c = threadIdx.x % 8, z0 = (threadIdx.x / 8) * PER;
-            const int nx = kx0 + c;
-            int rb = -1;
-            float rp = 0.0f, rk = 0.0f;   // FP32 sums over one run of at most a few dozen modes, flushed to FP64 bins
-            unsigned rc = 0;
-            const float mult = nx == 0 ? 1.0f : 2.0f;    // conjugate twin with k_x -> -k_x
             if (!nyq_y) {
-                for (int zz = 0; zz < PER; ++zz) {
-                    const int z = z0 + zz;
-                    if (z == L / 2) continue;
-                    const int nz = signed_bin(z, L);
-                    const int n2 = nx * nx + ny * ny + nz * nz;
-                    const int b = n2 == 0 ? -1 : (rb >= 0 && n2 >= lo[rb] && n2 < lo[rb + 1]) ? rb : power_bin(n2, lo, pw.nbins);
-                    if (b < 0) continue;
-                    if (b != rb) {
-                        if (rb >= 0) {
-                            atomicAdd(&psum[rb], (double)rp);
-                            atomicAdd(&ksum[rb], (double)rk);
-                            atomicAdd(&cnt[rb], (unsigned long long)rc);
-                        }
-                        rb = b;
-                        rp = 0.0f;
-                        rk = 0.0f;
-                        rc = 0;
-                    }
-                    const float2 v = cur[CT<L>::a2(z, c)];
-                    const float w = sinc2[nx] * sinc2[ky] * sinc2[z];
-                    rp += __fdividef(mult * (v.x * v.x + v.y * v.y) * pw.pnorm, w * w);
-                    rk += mult * pw.kf * sqrtf((float)n2);
-                    rc += nx == 0 ? 1u : 2u;
-                }
-            }
-            if (rb >= 0) {
-                atomicAdd(&psum[rb], (double)rp);
-                atomicAdd(&ksum[rb], (double)rk);
-                atomicAdd(&cnt[rb], (unsigned long long)rc);
+                constexpr int PER = L * 8 / T;
+                const int c = threadIdx.x % 8;
+                bin_column_run(kx0 + c, ny, (threadIdx.x / 8) * PER, PER, L, sinc2[kx0 + c] * sinc2[ky], sinc2, lo, pw,
+                               psum, ksum, cnt, [&](int z) { return cur[CT<L>::a2(z, c)]; });
             }
             __syncthreads();
             continue;

@@ -198,6 +198,8 @@ extern "C" int colapm_power_noalloc(const int* cell, const float* offset, long l
     pw.cnt = reinterpret_cast<unsigned long long*>(acc + 2 * nbins);
     pw.nbins = nbins;
     pw.pnorm = (float)(box * box * box / ((double)nm3 * (double)nm3));
+    pw.lga = (float)(0.5 * nbins / std::log2(h_edges[nbins] / h_edges[0]));
+    pw.lgb = (float)(nbins * std::log2(kf / h_edges[0]) / std::log2(h_edges[nbins] / h_edges[0]));
     NCK(launch_fz(nm, Z_POWER, spec, ZOut{}, tw, sinc2, 0, 1.0f, &pw, s));
     k_finish<<<(nbins + 127) / 128, 128, 0, s>>>(acc, nbins, out);
     NCK(cudaGetLastError());
