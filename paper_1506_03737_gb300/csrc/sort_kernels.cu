@@ -31,24 +31,67 @@ __device__ __forceinline__ unsigned bucket_of(float w, int nm, int xshift, int t
     return (tile << (2 * tshift)) + ((z & m) << tshift) + (y & m);
 }
 
-// Warp-aggregated increment: the lanes of a warp with the same bucket (in particle order a warp's
-// particles fill one or two buckets) make one atomic; each lane gets the old value plus its rank
-// among them. Lanes that have returned are not in the active mask.
-__device__ __forceinline__ unsigned warp_bucket_add(unsigned* ctr, unsigned b) {
+// Block-aggregated increment: the lanes of a warp with the same bucket are grouped (match_any; the
+// first lane leads), and the warp groups of the whole block with the same bucket are merged
+// through a small hash table in shared memory (keys, counts), so that each distinct bucket of the
+// block takes ONE global atomic and its slots are contiguous across the block's warps. With RANK, returns each valid
+// thread's slot (the bucket's old cursor + its rank in the block); every thread of the block must
+// call it (valid = false for threads without a particle). The table has twice as many slots as the
+// block has threads, so the bounded linear probing always finds the key or a free slot.
+constexpr int SC_T = 256;              // threads of the block-aggregated sort kernels
+constexpr int SC_H = 2 * SC_T;         // hash slots
+constexpr unsigned SC_EMPTY = 0xffffffffu;
+
+template <bool RANK>
+__device__ __forceinline__ size_t block_bucket_add(unsigned* ctr, unsigned b, bool valid) {
+    __shared__ unsigned keys[SC_H], cnt[SC_H], base[SC_H];
+    for (int i = threadIdx.x; i < SC_H; i += SC_T) {
+        keys[i] = SC_EMPTY;
+        cnt[i] = 0u;
+    }
+    __syncthreads();
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned peers = __match_any_sync(__activemask(), b);
-    const int leader = __ffs(peers) - 1;
-    unsigned base = 0;
-    if ((int)lane == leader) base = atomicAdd(ctr + b, (unsigned)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    return base + (unsigned)__popc(peers & ((1u << lane) - 1u));
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    unsigned peers = 0, off = 0;
+    int leader = 0, slot = 0;
+    if (valid) {
+        peers = __match_any_sync(act, b);
+        leader = __ffs(peers) - 1;
+        if ((int)lane == leader) {
+            unsigned h = (b * 2654435761u) % (unsigned)SC_H;
+            for (int i = 0; i < SC_H; ++i) {
+                const unsigned k = atomicCAS(&keys[h], SC_EMPTY, b);
+                if (k == SC_EMPTY || k == b) break;
+                h = h + 1 == (unsigned)SC_H ? 0u : h + 1;
+            }
+            slot = (int)h;
+            off = atomicAdd(&cnt[slot], (unsigned)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SC_H; i += SC_T) {
+        const unsigned k = keys[i];
+        if (k != SC_EMPTY) {
+            const unsigned o = atomicAdd(ctr + k, cnt[i]);
+            if (RANK) base[i] = o;
+        }
+    }
+    if (!RANK) return 0;
+    __syncthreads();
+    size_t d = ~(size_t)0;
+    if (valid) {
+        unsigned bs = (int)lane == leader ? base[slot] + off : 0u;
+        bs = __shfl_sync(peers, bs, leader);
+        d = bs + (unsigned)__popc(peers & ((1u << lane) - 1u));
+    }
+    return d;
 }
 
-__global__ void k_sort_count(const float4* __restrict__ pos, size_t np3, int nm, int xshift, int tshift,
-                             unsigned* __restrict__ cnt) {
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np3) return;
-    warp_bucket_add(cnt, bucket_of(__ldg(&pos[p].w), nm, xshift, tshift));
+__global__ void __launch_bounds__(SC_T) k_sort_count(const float4* __restrict__ pos, size_t np3, int nm, int xshift,
+                                                     int tshift, unsigned* __restrict__ cnt) {
+    const size_t p = (size_t)blockIdx.x * SC_T + threadIdx.x;
+    const bool valid = p < np3;
+    block_bucket_add<false>(cnt, valid ? bucket_of(__ldg(&pos[p].w), nm, xshift, tshift) : 0u, valid);
 }
 
 // Exclusive scan of cnt[0..n) in tiles of SCAN_TILE: tile sums first, then the scan within tiles
@@ -155,16 +198,20 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(const unsigned* cnt, size
 }
 
 // Move every particle to the next free slot of its bucket (cursor[] starts at the bucket offsets).
-__global__ void k_sort_scatter(const float4* __restrict__ pos, const float* __restrict__ mom,
-                               const float* __restrict__ psi1, const float* __restrict__ psi2,
-                               const int* __restrict__ id, size_t np3, int nm, int xshift, int tshift,
-                               unsigned* __restrict__ cursor, float4* __restrict__ pos_o, float* __restrict__ mom_o,
-                               float* __restrict__ psi1_o, float* __restrict__ psi2_o, int* __restrict__ id_o,
-                               int* err) {
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np3) return;
-    const float4 P = __ldcs(pos + p);
-    const size_t d = warp_bucket_add(cursor, bucket_of(P.w, nm, xshift, tshift));
+// The slots of one bucket taken by one block are contiguous (block-aggregated cursors), so that the
+// block's writes to each array come in runs as long as its particles of that bucket.
+__global__ void __launch_bounds__(SC_T) k_sort_scatter(const float4* __restrict__ pos, const float* __restrict__ mom,
+                                                       const float* __restrict__ psi1, const float* __restrict__ psi2,
+                                                       const int* __restrict__ id, size_t np3, int nm, int xshift,
+                                                       int tshift, unsigned* __restrict__ cursor,
+                                                       float4* __restrict__ pos_o, float* __restrict__ mom_o,
+                                                       float* __restrict__ psi1_o, float* __restrict__ psi2_o,
+                                                       int* __restrict__ id_o, int* err) {
+    const size_t p = (size_t)blockIdx.x * SC_T + threadIdx.x;
+    const bool valid = p < np3;
+    const float4 P = valid ? __ldcs(pos + p) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const size_t d = block_bucket_add<true>(cursor, valid ? bucket_of(P.w, nm, xshift, tshift) : 0u, valid);
+    if (!valid) return;
     if (d >= np3) {   // cannot happen with consistent counts; guards the writes below
         atomicOr(err, 8);
         return;
@@ -224,11 +271,11 @@ cudaError_t launch_sort(SortBuffers b, size_t np3, int nm, int tshift, cudaStrea
     const size_t nb = sort_buckets(nm), nt = sort_tiles(nm);
     cudaError_t e = cudaMemsetAsync(b.cnt, 0, nb * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    k_sort_count<<<blocks(np3, 256), 256, 0, s>>>(b.pos, np3, nm, xs, tshift, b.cnt);
+    k_sort_count<<<blocks(np3, SC_T), SC_T, 0, s>>>(b.pos, np3, nm, xs, tshift, b.cnt);
     k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, s>>>(b.cnt, nb, b.tile_sum);
     k_scan_sums<<<1, SCAN_T, 0, s>>>(b.tile_sum, (int)nt);
     k_scan_apply<<<(unsigned)nt, SCAN_T, 0, s>>>(b.cnt, nb, b.tile_sum, b.cnt);   // counts -> cursors in place
-    k_sort_scatter<<<blocks(np3, 256), 256, 0, s>>>(b.pos, b.mom, b.psi1, b.psi2, b.id, np3, nm, xs, tshift, b.cnt, b.pos_o,
+    k_sort_scatter<<<blocks(np3, SC_T), SC_T, 0, s>>>(b.pos, b.mom, b.psi1, b.psi2, b.id, np3, nm, xs, tshift, b.cnt, b.pos_o,
                                                      b.mom_o, b.psi1_o, b.psi2_o, b.id_o, b.err);
     return cudaGetLastError();
 }
