@@ -337,8 +337,8 @@ __global__ void __launch_bounds__(MW_T) k_multi_gather_kick_drift(const MockWork
 // half a PM cell). Integer part of i nm / np and its exact fractional remainder (0 when np divides nm;
 // a multiple of nm / np otherwise, i.e. of 1/2 or 1/4 for the coarse meshes).
 __device__ __forceinline__ void lattice_site(int i, int np, int nm, int& base, float& frac) {
-    const long long t = (long long)i * nm;
-    base = (int)(t / np);
+    const int t = i * nm;   // < 2^20 for the supported sizes (np, nm <= 1024): 32-bit division
+    base = t / np;
     frac = (float)(t % np) / (float)np;
 }
 
@@ -350,7 +350,8 @@ __global__ void k_init_particles(float4* __restrict__ pos, float* __restrict__ m
     const size_t np3 = (size_t)np * np * np;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
-    const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
+    const unsigned up = (unsigned)p, unp = (unsigned)np;   // np^3 <= 2^30: 32-bit divisions
+    const int site[3] = {(int)(up % unp), (int)((up / unp) % unp), (int)(up / (unp * unp))};
     int cell[3];
     float o[3];
 #pragma unroll
@@ -461,7 +462,8 @@ __global__ void k_export_displacement(const float4* __restrict__ pos, int np, in
     const float4 P = pos[p];
     const unsigned c = __float_as_uint(P.w), u = (unsigned)nm;
     const int cc[3] = {(int)(c % u), (int)((c / u) % u), (int)(c / (u * u))};
-    const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
+    const unsigned up = (unsigned)p, unp = (unsigned)np;   // np^3 <= 2^30: 32-bit divisions
+    const int site[3] = {(int)(up % unp), (int)((up / unp) % unp), (int)(up / (unp * unp))};
     const float off[3] = {P.x, P.y, P.z};
     const int h = nm / 2;
 #pragma unroll
@@ -483,7 +485,8 @@ __global__ void k_import_displacement(float4* __restrict__ pos, int np, int nm, 
     const size_t np3 = (size_t)np * np * np;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np3) return;
-    const int site[3] = {(int)(p % np), (int)((p / np) % np), (int)(p / ((size_t)np * np))};
+    const unsigned up = (unsigned)p, unp = (unsigned)np;   // np^3 <= 2^30: 32-bit divisions
+    const int site[3] = {(int)(up % unp), (int)((up / unp) % unp), (int)(up / (unp * unp))};
     int cell[3];
     float o[3];
 #pragma unroll
