@@ -382,8 +382,9 @@ int colapm_batch_streams(const colapm_batch* b);
  * of each mock, and one multi-mock gather-kick-drift. The two multi-mock kernels are persistent:
  * their CTAs take work items (mock, chunk of 256 particles) from a ticket counter across all the
  * mocks, whatever their sizes. on = 0: each mock runs its ICs, steps and P(k) in turn (on worker
- * streams). Both give the same results bit for bit (the per-particle code is the same and the
- * fixed-point deposit does not depend on order). The next run captures the chosen schedule.
+ * streams). Both give the same particles bit for bit (the per-particle code is the same and the
+ * fixed-point deposit does not depend on order), and the same P(k) up to the order of its FP64 bin
+ * sums, which are atomic and so not fixed from run to run (about 1e-16 relative). The next run captures the chosen schedule.
  * COLAPM_E_ARG for other values. */
 int colapm_batch_set_lockstep(colapm_batch* b, int on);
 

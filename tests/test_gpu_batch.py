@@ -96,10 +96,11 @@ def test_autotune_preserves_state_and_results(C):
         C.colapm_destroy(b)
 
 
-def test_lockstep_and_per_mock_schedules_agree_bit_for_bit(C):
+def test_lockstep_and_per_mock_schedules_agree(C):
     """The lockstep schedule (multi-mock persistent deposit and gather over work items of every
-    mock, uneven sizes and step counts) against each mock run on its own, in one batch: identical
-    P(k), replay after replay (the ticket counters reset themselves)."""
+    mock, uneven sizes and step counts) against each mock run on its own, in one batch: the same
+    mode counts and the same P(k) up to the order of the FP64 bin sums (atomic, so not fixed from
+    run to run), replay after replay (the ticket counters reset themselves)."""
     params = [C.default_params(np=a, nm=b, box=L, seed=700 + i, n_steps=4 + (i % 3)) for i, (a, b, L) in enumerate(MOCKS)]
     b = C.colapm_batch_create(params, nstreams=2)
     try:
@@ -111,8 +112,8 @@ def test_lockstep_and_per_mock_schedules_agree_bit_for_bit(C):
         C.colapm_batch_set_lockstep(b, False)
         k2, p2, n2 = C.colapm_batch_run(b, len(params), nbins, seeds=seeds)
         assert np.array_equal(n1, n2)
-        assert np.array_equal(p1, p2, equal_nan=True) and np.array_equal(k1, k2, equal_nan=True)
-        assert np.array_equal(p1, p1b, equal_nan=True)
+        for a, b_ in ((p1, p2), (k1, k2), (p1, p1b), (k1, k1b)):
+            assert np.allclose(a, b_, rtol=1e-12, atol=0.0, equal_nan=True)
         assert C.LIB.colapm_batch_set_lockstep(b, 2) == C.LIB.colapm_batch_set_lockstep(None, 1) != 0
     finally:
         C.colapm_batch_destroy(b)

@@ -422,8 +422,8 @@ def test_finalize_adds_lpt_momentum(C):
 def test_cell_order_changes_no_result(C, np_, nm, every, tiles):
     """Reordering the particle arrays by cell (by rows, or tile by tile with the tiled deposit) is
     invisible: every step is per particle or an exact integer sum, so runs with and without it give
-    bit-identical catalogues, states, LPT fields, densities, spectra and finalized momenta, in
-    particle-id order."""
+    bit-identical catalogues, states, LPT fields, densities and finalized momenta, in particle-id
+    order, and the same spectra up to the order of their atomic FP64 bin sums."""
     kw = dict(np=np_, nm=nm, box=200.0, seed=13, n_steps=6)
     a, b = Sim(C, **kw), Sim(C, **kw)
     try:
@@ -450,7 +450,8 @@ def test_cell_order_changes_no_result(C, np_, nm, every, tiles):
         assert np.array_equal(a.density(), b.density())
         ka, pka, na = C.colapm_power(a.ctx, 30)
         kb, pkb, nb = C.colapm_power(b.ctx, 30)
-        assert np.array_equal(na, nb) and np.array_equal(pka, pkb, equal_nan=True)
+        assert np.array_equal(na, nb)   # P(k): up to the order of the atomic FP64 bin sums
+        assert np.allclose(pka, pkb, rtol=1e-12, atol=0.0, equal_nan=True)
         psi_a, psi_b = np.empty((n, 3), np.float32), np.empty((n, 3), np.float32)
         C.colapm_get_displacement(a.ctx, psi_a)
         C.colapm_get_displacement(b.ctx, psi_b)
