@@ -34,3 +34,15 @@ def test_roofline_per_call_time_and_traffic_scope():
     assert r["kernel"] == "poisson"
     assert abs(r["achieved"] - 12 * 1024 ** 3 / 6e-3 / 1e9) <= 1e-9 * r["achieved"]
     assert bench.roofline(ms, n, 512, 512, 6691.5)["traffic"] is None   # not N_m = 2 N_p
+
+
+def test_roofline_traffic_of_a_kernel_that_runs_only_at_1024():
+    """The force z pass at 1024^3 is another kernel (each task on a pair of lanes) than the one
+    measured at 512^3: its traffic is its own 1024^3 measurement, not the scaled 512^3 one."""
+    ms, n = phases()
+    ms["poisson"] = 90.0
+    r = bench.roofline(ms, n, 512, 1024, 6786.2)
+    assert r["kernel"] == "poisson" and r["traffic"] == bench.DRAM_1024["poisson"]
+    assert 1.0 <= r["traffic"] / r["alg_bytes"] < 1.1
+    r = bench.roofline(ms, n, 256, 512, 6786.2)
+    assert r["traffic"] == bench.DRAM_512["poisson"]
