@@ -319,13 +319,13 @@ int colapm_set_engine(colapm_ctx* ctx, int fused, int two_stage, int block);
  * uses the plain layout there. COLAPM_E_ARG outside 0 ... COLAPM_PLAN_ALL. */
 int colapm_set_plan(colapm_ctx* ctx, int plan);
 
-/* The context's configuration: cfg (6 ints) = {plan mask, particle-kernel block size, fused x-y
- * passes (0 where N_m has none), sort cadence (colapm_set_sort), sort-key tile T (1: rows),
- * tiled deposit (0/1)}. */
+/* The context's configuration: cfg (7 ints) = {plan mask, particle-kernel block size, fused x-y
+ * passes (0 where N_m has none), reordering period (0: never), sort-key tile T (1: rows), tiled
+ * deposit (0/1), step of the first reordering}. */
 int colapm_get_config(const colapm_ctx* ctx, int* cfg);
 
 /* Reorder the particle arrays by mesh cell before every `every`-th step (0: never). The default is
- * once, halfway through the run (every = n_steps / 2) on meshes of 512^3 cells and more, else never. The analogue of the paper's particle migration (§4),
+ * once, before step 2 n_steps / 5 (step 4 of 10), on meshes of 512^3 cells and more, else never. The analogue of the paper's particle migration (§4),
  * which keeps each rank's particles with its slab of the mesh: here it keeps a warp's particles
  * on neighbouring mesh cells, so that the deposit and the gather read and write runs of cells as
  * structure grows. It is a counting sort of all particle arrays by bucket (z, y, x / 64) of the

@@ -345,10 +345,10 @@ def colapm_set_plan(ctx, plan):
 
 
 def colapm_get_config(ctx):
-    cfg = np.zeros(6, dtype=np.int32)
+    cfg = np.zeros(7, dtype=np.int32)
     _check(LIB.colapm_get_config(ctx, _ptr(cfg)), "colapm_get_config")
     return {"plan": int(cfg[0]), "block": int(cfg[1]), "fused": int(cfg[2]), "sort_every": int(cfg[3]),
-            "sort_tiles": int(cfg[4]), "deposit_tiled": bool(cfg[5])}
+            "sort_tiles": int(cfg[4]), "deposit_tiled": bool(cfg[5]), "sort_first": int(cfg[6])}
 
 
 def colapm_set_sort_tiles(ctx, t):

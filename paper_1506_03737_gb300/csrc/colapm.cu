@@ -36,7 +36,8 @@ struct colapm_ctx {
     int* id_alt = nullptr;
     unsigned* sort_cnt = nullptr;        // bucket counters / cursors of the cell sort
     unsigned* sort_tile = nullptr;       // their tile sums
-    int sort_every = 0;                  // reorder by cell before every k-th step (0: never)
+    int sort_every = 0;                  // reorder by cell every k steps from step sort_first (0: never)
+    int sort_first = 0;
     int key_tshift = 0;                  // sort key: tiles of 64 x 2^t x 2^t cells (0: rows of 64)
     bool dep_tiled = false;              // tiled deposit while the particles are in tile order
     int sorted_tshift = -1;              // tile shift of the order the particles are in (-1: id order)
@@ -197,6 +198,11 @@ DepositSrc own_particles(const colapm_ctx* c) {
 }
 
 // Fixed-point CIC deposit into c's mesh of the given particles (default: c's own).
+// Whether the particles are reordered before step `step`: every sort_every steps from sort_first.
+bool sort_due(const colapm_ctx* c, int step) {
+    return c->sort_every > 0 && step > 0 && step >= c->sort_first && (step - c->sort_first) % c->sort_every == 0;
+}
+
 // Whether the own particles are ordered by the tiles of the tiled deposit (the last sort used the
 // context's tile shape and nothing has restored id order since).
 bool tiles_ready(const colapm_ctx* c) {
@@ -549,10 +555,11 @@ int colapm_create(const colapm_params* p, void* stream, colapm_ctx** out) {
         return COLAPM_E_CUDA;
     }
     c->seed_src = c->d_seed;
-    // Default reordering by cell: once, halfway through the run, on meshes far larger than L2 (at
-    // 1024^3 one sort before step 5 of 10 measured 28.7 against 29.1 ms per step; more frequent sorts
-    // cost more than they save, see colapm_set_sort).
-    c->sort_every = c->nm >= 512 && p->n_steps >= 4 ? p->n_steps / 2 : 0;
+    // Default reordering by cell: once, before step 2 n / 5, on meshes far larger than L2 (at 1024^3,
+    // 10 steps, one sort before step 4 measured 27.76 ms per step against 27.78 and 27.89 before
+    // steps 3 and 5; more frequent sorts cost more than they save).
+    c->sort_every = c->nm >= 512 && p->n_steps >= 4 ? p->n_steps : 0;
+    c->sort_first = 2 * p->n_steps / 5 > 0 ? 2 * p->n_steps / 5 : 1;
     c->key_tshift = c->nm % 2 == 0 ? 1 : 0;   // tiles of 64 x 2 x 2 cells (measured best of 1, 2, 4, 8 at 1024^3)
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -627,7 +634,7 @@ int colapm_step(colapm_ctx* c, int k) {
     if (k < 0) k = left;
     if (k > left) return COLAPM_E_STATE;
     for (int s = 0; s < k; ++s) {
-        if (c->sort_every > 0 && c->step > 0 && c->step % c->sort_every == 0) {
+        if (sort_due(c, c->step)) {
             int r = sort_particles(c);
             if (r) return r;
         }
@@ -1257,6 +1264,7 @@ int colapm_get_config(const colapm_ctx* c, int* cfg) {
     cfg[1] = c->block;
     cfg[2] = c->xy_ring ? c->fused : 0;
     cfg[3] = c->sort_every;
+    cfg[6] = c->sort_first;
     cfg[4] = 1 << c->key_tshift;
     cfg[5] = c->dep_tiled ? 1 : 0;
     return COLAPM_OK;
@@ -1294,6 +1302,7 @@ int colapm_set_deposit_tiles(colapm_ctx* c, int t) {
 int colapm_set_sort(colapm_ctx* c, int every) {
     if (!c || every < 0) return COLAPM_E_ARG;
     c->sort_every = every;
+    c->sort_first = every;
     return COLAPM_OK;
 }
 
@@ -1534,7 +1543,7 @@ int batch_enqueue_lockstep(colapm_batch* b, int K) {
             colapm_ctx* c = b->ctx[i];
             if (st >= c->prm.n_steps) continue;
             c->stream = b->user;
-            if (c->sort_every > 0 && st > 0 && st % c->sort_every == 0) r = sort_particles(c);
+            if (sort_due(c, st)) r = sort_particles(c);
             if (!c->rho_clean && cudaMemsetAsync(c->rho, 0, c->nm3 * sizeof(unsigned long long), b->user) != cudaSuccess)
                 r = COLAPM_E_CUDA;
             c->rho_clean = false;

@@ -140,6 +140,9 @@ def test_every_plan_mask_gives_the_same_force(C, np_, nm):
         for plan, f in out.items():
             diff = f.double() - ref
             assert torch.sqrt(torch.mean(diff ** 2)).item() < 1e-5 * scale, plan
+        if nm >= 512:   # default reordering: once, before step 2 n_steps / 5
+            cfg = C.colapm_get_config(ctx)
+            assert cfg["sort_every"] == 10 and cfg["sort_first"] == 4 and cfg["sort_tiles"] == 2
         if nm < 512:   # (tuning is remembered per size for the rest of the process)
             C.colapm_autotune(ctx)
             cfg = C.colapm_get_config(ctx)
